@@ -1,0 +1,347 @@
+"""Benchmark of the fused generate-and-sketch hot path.
+
+One step = the left sketches Y = S A of the tall-skinny workload
+(A 2^20 x 512 FP32 ~ N(0,1), k = 2048) with a Rademacher and with a
+Gaussian S, both regenerated inside the kernels from Philox4x32-10.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x2|fp32]
+                  [--impl ours|reference] [--workload C2|C1]
+
+Prints ONE JSON line (rank 0).  `value` is useful TFLOP/s (2 k m n per
+sketch) over the whole job; `roofline` describes the dominant kernel (the
+fused sketch kernel) timed with CUDA events recorded by the library's
+measurement hook around each of its launches; `e2e` repeats the step
+through the host-buffer entry points (A copied host->device and Y copied
+back inside the timed region); `cpu_baseline` is the CPU oracle on a
+bounded column sample.  `--impl reference` times the CPU oracle alone.
+Under torchrun each rank sketches its own copy of the workload (independent
+problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (m, n, k, dists)
+    "C2": (1 << 20, 512, 2048, (1, 0)),
+    "C1": (4096, 256, 64, (0,)),
+}
+DIST_NAME = {0: "gaussian", 1: "rademacher", 2: "uniform"}
+METRIC = "fused gen+sketch TFLOP/s and % roofline vs plain FP32; served p50/p99 latency"
+L2_BYTES = 129 * 2**20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(m, n, k, dists, a_cols, seed, rows, nthreads=None):
+    """Time the CPU oracle on `rows` rows x a_cols.shape[1] columns of Y for
+    each distribution.  Returns (seconds, useful flops, threads)."""
+    import oracle
+    nthreads = nthreads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    for d in dists:
+        oracle.apply_left(seed, d, 0, k, a_cols, nthreads=nthreads, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * rows * m * a_cols.shape[1] * len(dists), nthreads
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on a bounded sample per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    from paper_2603_20966_gb300.workloads import gaussian_matrix
+    m, n, k, dists = WORKLOADS[args.workload]
+    ncols, rows = (2, 512) if args.workload == "C2" else (n, k)
+    a_cols = gaussian_matrix(m, ncols, 1, device="cpu").numpy()
+    for _ in range(args.warmup):
+        oracle_sample(m, n, k, dists, a_cols, 7, rows)
+    tot, flops, threads = 0.0, 0.0, 1
+    for _ in range(args.steps):
+        dt, fl, threads = oracle_sample(m, n, k, dists, a_cols, 7, rows)
+        tot += dt
+        flops += fl
+    value = flops / tot / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} left sketch A {m}x{n} k={k} "
+                   f"dists={[DIST_NAME[d] for d in dists]}", "m": m, "n": n, "k": k},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{rows} of {k} rows x {ncols} of {n} columns of Y per "
+                                   f"distribution per step (FP64 accumulation)"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2603_20966_gb300 as P
+    from paper_2603_20966_gb300.workloads import gaussian_matrix
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    m, n, k, dists = WORKLOADS[args.workload]
+    form = {"fp32": P.SK_FP32, "bf16x2": P.SK_BF16X2}[args.form]
+    stream = torch.cuda.current_stream(dev)
+
+    A = gaussian_matrix(m, n, 1 + rank, device=dev)
+    Ys = {d: torch.empty((k, n), dtype=torch.float32, device=dev) for d in dists}
+    hs = {}
+    for d in dists:
+        hs[d] = P.sk_create(7, d, k)
+        P.sk_set_precision(hs[d], form)
+
+    def step():
+        for d in dists:
+            P.sk_apply_left(hs[d], A, m, n, n, Ys[d], n, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    for d in dists:
+        st = P.sk_stream_status(hs[d], stream)
+        if st != 0:
+            raise RuntimeError(f"device status after warm-up: {P.status_string(st)}")
+
+    # per-launch events of the fused kernel, recorded by the library hook
+    nl = args.steps * len(dists)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nl)]
+    for a, b in ev:  # create the underlying events before handing them out
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    launches0 = P.sk_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    i = 0
+    for _ in range(args.steps):
+        for d in dists:
+            P.sk_profile_events(hs[d], ev[i][0], ev[i][1])
+            P.sk_apply_left(hs[d], A, m, n, n, Ys[d], n, stream)
+            i += 1
+    t_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = P.sk_launch_count() - launches0
+    if world > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    for d in dists:
+        P.sk_profile_events(hs[d], None, None)
+        st = P.sk_stream_status(hs[d], stream)
+        if st != 0:
+            raise RuntimeError(f"device status after timing: {P.status_string(st)}")
+    ms = t_start.elapsed_time(t_stop)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    flops_per_sketch = 2.0 * k * m * n
+    flops_step = flops_per_sketch * len(dists)
+    value = world * flops_step * args.steps / (ms * 1e-3) / 1e12
+
+    pk, pk_kind = peaks()
+    avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
+    if form == P.SK_FP32:
+        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops_per_sketch / avg_kernel_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x "
+                                                "max SM clock"}
+    else:
+        mma = 2 * flops_per_sketch  # split-A: two BF16 MMA passes
+        peak = pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": mma / avg_kernel_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_kind": f"{pk_kind} bf16 burst",
+                "note": "achieved counts both split-A MMA passes (4 k m n flop per sketch)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms_by_dist"] = {DIST_NAME[d]: statistics.mean(kernel_ms[j::len(dists)])
+                                 for j, d in enumerate(dists)}
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A)
+        Y_host = {d: torch.empty((k, n), dtype=torch.float32, pin_memory=True) for d in dists}
+
+        def e2e_step():
+            for d in dists:
+                P.sk_apply_left_host(hs[d], A_host, m, n, n, Y_host[d], n, stream)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_step()
+        if world > 1:
+            tdist.barrier()
+        e_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": len(dists) * m * n * 4,
+               "d2h_bytes_per_step": len(dists) * k * n * 4, "steps": e_steps,
+               "ms_per_step": dt / e_steps * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ncols, rows = (16, 2048) if args.workload == "C2" else (n, k)
+        cols = np.linspace(0, n - 1, ncols).astype(np.int64)
+        a_cols = A[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
+        dt, fl, threads = oracle_sample(m, n, k, dists, a_cols, 7, rows)
+        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"{rows} of {k} rows x {ncols} of {n} columns of Y for each of "
+                         f"{[DIST_NAME[d] for d in dists]} (FP64 accumulation), "
+                         f"{dt:.1f} s; rate extrapolates to the full workload"}
+
+    for d in dists:
+        P.sk_destroy(hs[d])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16x2": "bf16x2"}[args.form], "data": "synthetic",
+            "config": {"workload": f"{args.workload} left sketch A {m}x{n} FP32 N(0,1), k={k}, "
+                                   f"S {[DIST_NAME[d] for d in dists]} Philox4x32-10 seed 7",
+                       "m": m, "n": n, "k": k, "form": args.form,
+                       "l2": f"inputs larger than L2 (A {m * n * 4 / 2**30:.2f} GiB)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "bf16x2"])
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

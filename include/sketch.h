@@ -1,0 +1,173 @@
+/*
+ * sketch.h -- C ABI of the GB300 random-sketch library.
+ *
+ * The library computes sketches of a dense FP32 matrix A by a dense random
+ * matrix whose entries are regenerated on the GPU from a counter-based
+ * generator instead of being stored or read from memory:
+ *
+ *   left  sketch  Y[k x n] = S[k x m] * A[m x n]
+ *   right sketch  Y[m x k] = A[m x n] * Omega,   Omega = S^T, S[k x n]
+ *
+ * with S(r, c) = s * q(g(r, c)), s = fl32(1/sqrt(k)), g(r, c) a Gaussian
+ * N(0,1), Rademacher +-1 or uniform [0,1) draw that is a pure function of
+ * (seed, r, c), and q the storage precision of the generated operand.
+ *
+ * Paper: arXiv 2603.20966 (Al Daas et al., "Communication Lower Bounds and
+ * Algorithms for Sketching with Random Dense Matrices").  The product is the
+ * sketch B = A Omega of Sec. 1 and Sec. 3; the left form is the transposed
+ * computation the paper notes after Theorem 2 (Omega^T A^T).  Generating the
+ * random operand where it is consumed, with a shared seed, is the paper's
+ * "generate Omega redundantly instead of communicating it" (Sec. 6.2 and
+ * Alg. 1 GenRandom); on one GPU it becomes "generate S tiles in shared
+ * memory instead of reading S from HBM".
+ *
+ * Conventions for every call:
+ *  - Matrices are row-major with a leading dimension (elements between
+ *    consecutive rows).  Pointers named A, Y, out are DEVICE pointers unless
+ *    the function name ends in _host.  The caller owns every buffer it
+ *    passes; the library never frees or retains them past the call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is asynchronous on that stream; a return of SK_OK means the work
+ *    was validated and enqueued.
+ *  - Host-detectable errors return immediately, enqueue nothing and leave
+ *    outputs untouched: SK_EINVAL for a NULL handle/pointer, a size <= 0,
+ *    a leading dimension smaller than the row length, or an index beyond
+ *    2^32; SK_EUNSUPPORTED for a precision/size combination a form does not
+ *    implement; SK_ECUDA when a CUDA call fails (cudaGetLastError is
+ *    cleared).  Errors raised on the device (a bounded wait that gave up,
+ *    a bounds check) are recorded in a per-handle status word that
+ *    sk_stream_status() reads.
+ *  - Determinism: identical (seed, dist, k, precision, A) give bit-identical
+ *    Y on the same GPU model, independent of stream, batch or serving mix.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef SKETCH_H_
+#define SKETCH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SK_OK = 0,
+  SK_EINVAL = 1,        /* bad argument */
+  SK_ENOMEM = 2,        /* device or host allocation failed */
+  SK_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+  SK_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  SK_EBUDGET = 5,       /* request exceeds the serving memory budget */
+  SK_EUNSUPPORTED = 6,  /* combination not implemented by the selected form */
+  SK_EBUSY = 7,         /* result not ready yet (serving poll) */
+  SK_ECANCELLED = 8     /* request cancelled before completion */
+} sk_status;
+
+/* Distribution of g(r, c).  Gaussian is the paper's theoretical choice
+ * (Sec. 1, "Gaussian random matrices"); uniform is what its experiments
+ * draw with Philox (Sec. 6.2); Rademacher +-1 is exact in every precision. */
+typedef enum { SK_GAUSSIAN = 0, SK_RADEMACHER = 1, SK_UNIFORM = 2 } sk_dist;
+
+/* Arithmetic form of the product.
+ *  SK_FP32     FP32 generated operand, FP32 FMA on the CUDA cores.
+ *  SK_BF16X2   generated operand rounded to BF16, A split into BF16 hi + lo
+ *              parts (hi = bf16(a), lo = bf16(a - hi)), two tensor-core MMAs
+ *              per tile with FP32 accumulation in tensor memory.
+ *  SK_FP8E4M3  generated operand rounded to E4M3, A quantised to E4M3 with
+ *              one power-of-two scale per 32 consecutive elements along the
+ *              contracted dimension (block-scaled tensor-core MMA).
+ * The 1/sqrt(k) scale is one FP32 multiply in every form's epilogue. */
+typedef enum { SK_FP32 = 0, SK_BF16X2 = 1, SK_FP8E4M3 = 2 } sk_precision;
+
+typedef struct sk_sketch* sk_handle;
+
+/* Create a sketch operator.  seed: the Philox key (low 32 bits -> key word
+ * 0, high 32 bits -> key word 1).  dist: an sk_dist.  k: sketch size
+ * (rows of S), 1 <= k <= 2^31.  *out receives the handle.  Allocates a few
+ * bytes of device memory for the status word on the current device; all
+ * later calls on the handle must run with that device current.
+ * Errors: SK_EINVAL (bad dist/k/out), SK_ENOMEM, SK_ECUDA. */
+sk_status sk_create(uint64_t seed, int dist, int64_t k, sk_handle* out);
+
+/* Select the arithmetic form (an sk_precision) for later apply calls.
+ * Default SK_FP32.  Errors: SK_EINVAL. */
+sk_status sk_set_precision(sk_handle h, int precision);
+
+/* Read back the handle's parameters (any pointer may be NULL). */
+sk_status sk_get_info(sk_handle h, uint64_t* seed, int* dist, int64_t* k, int* precision,
+                      float* scale);
+
+/* Left sketch Y[k x n] = S[k x m] A[m x n] (A: m x n, leading dim lda >= n;
+ * Y: k x n, leading dim ldy >= n; both device pointers, FP32).  S(r, c)
+ * for r < k, c < m.  Requires m < 2^32.  The tensor-core forms additionally
+ * require A and Y 16-byte aligned and lda, ldy multiples of 4 (SK_EINVAL
+ * otherwise).  Y is fully overwritten.  A and Y must not overlap. */
+sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda, float* Y,
+                        int64_t ldy, void* stream);
+
+/* Right sketch Y[m x k] = A[m x n] S^T (S: k x n, S(r, c) for r < k,
+ * c < n).  Same conventions as sk_apply_left; requires n < 2^32. */
+sk_status sk_apply_right(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
+                         float* Y, int64_t ldy, void* stream);
+
+/* The same two products with HOST buffers: A is copied to the device, the
+ * sketch computed, and Y copied back before the call returns (the call
+ * synchronises `stream`).  Pinned host memory gives full copy bandwidth;
+ * pageable memory works.  Device staging memory is owned by the handle and
+ * reused across calls.  Errors as above plus SK_ENOMEM. */
+sk_status sk_apply_left_host(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
+                             float* Y, int64_t ldy, void* stream);
+sk_status sk_apply_right_host(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
+                              float* Y, int64_t ldy, void* stream);
+
+/* Debugging: write the block S(row0 .. row0+rows-1, col0 .. col0+cols-1)
+ * to the device buffer `out` (leading dim ld >= cols).  fmt selects the
+ * stored value set and element type: SK_FP32 -> float g (or fl32(s*g)
+ * when scaled != 0); SK_BF16X2 -> uint16 bf16(g); SK_FP8E4M3 -> uint8
+ * e4m3(g).  scaled != 0 is valid only with SK_FP32.  row0+rows <= 2^32 and
+ * col0+cols <= 2^32.  The fused kernels never call this; S never exists in
+ * device memory on the apply paths. */
+sk_status sk_materialize(sk_handle h, int64_t row0, int64_t col0, int64_t rows, int64_t cols,
+                         int fmt, int scaled, void* out, int64_t ld, void* stream);
+
+/* Scratch memory: bytes of device workspace an apply call with these sizes
+ * needs in the handle's current form (side 0 = left, 1 = right), or 0.
+ * sk_set_workspace lends the handle a caller-owned device buffer of `bytes`
+ * (16-byte aligned; NULL/0 returns to handle-owned scratch, which the
+ * handle allocates with cudaMalloc on first need and frees in sk_destroy).
+ * A lent buffer must stay valid until every call that used it completed. */
+sk_status sk_workspace_size(sk_handle h, int side, int64_t m, int64_t n, size_t* bytes);
+sk_status sk_set_workspace(sk_handle h, void* ptr, size_t bytes);
+
+/* Synchronise `stream`, then return and clear the handle's device status
+ * word: SK_OK, SK_ETIMEOUT (a bounded wait gave up; outputs of the affected
+ * call are undefined), or SK_ECUDA if the stream reported an error. */
+sk_status sk_stream_status(sk_handle h, void* stream);
+
+/* Release the handle and the device memory it owns.  Waits for nothing:
+ * the caller must ensure no enqueued work still uses it. */
+sk_status sk_destroy(sk_handle h);
+
+/* Measurement hook: when both events are non-NULL (cudaEvent_t created by
+ * the caller on the handle's device), every later apply call records
+ * `start_event` on its stream immediately before the launch of its main
+ * fused kernel and `stop_event` immediately after it, so the caller can
+ * read that kernel's duration with cudaEventElapsedTime.  NULL, NULL turns
+ * the hook off.  The events stay owned by the caller. */
+sk_status sk_profile_events(sk_handle h, void* start_event, void* stop_event);
+
+/* Number of kernels this library has launched in the calling process
+ * (all handles, all devices), for launch accounting. */
+uint64_t sk_launch_count(void);
+
+/* Static human-readable name of a status code. */
+const char* sk_status_string(int status);
+
+/* Library version as an integer MAJOR*10000 + MINOR*100 + PATCH. */
+int sk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKETCH_H_ */

@@ -76,6 +76,9 @@ def lib():
             L.orc_scale.restype = ctypes.c_float
             L.orc_generate.argtypes = [u64, i32, i32, u32, i64, i64, i64, i64, vp, i64]
             L.orc_generate.restype = i32
+            L.orc_apply_left_rows.argtypes = [u64, i32, i32, i64, i64, i64, vp, i64, i64, i64, vp,
+                                              i64, vp, i64, i32]
+            L.orc_apply_left_rows.restype = i32
             for f in (L.orc_apply_left, L.orc_apply_right):
                 f.argtypes = [u64, i32, i32, i64, vp, i64, i64, i64, vp, i64, vp, i64, i32]
                 f.restype = i32
@@ -154,8 +157,9 @@ def materialize_scaled(seed: int, dist: int, prec: int, k: int, row0: int, col0:
 
 
 def apply_left(seed: int, dist: int, prec: int, k: int, A: np.ndarray, cols=None,
-               nthreads: int | None = None) -> np.ndarray:
-    """Y = S[k x m] A[m x n] in FP64 (optionally only the columns ``cols``)."""
+               nthreads: int | None = None, rows: tuple[int, int] | None = None) -> np.ndarray:
+    """Y = S[k x m] A[m x n] in FP64 (optionally only the columns ``cols`` and
+    the rows ``rows = (row0, count)``)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     m, n = A.shape
     if cols is None:
@@ -163,10 +167,11 @@ def apply_left(seed: int, dist: int, prec: int, k: int, A: np.ndarray, cols=None
     else:
         idx = np.ascontiguousarray(cols, dtype=np.int64)
         nidx = idx.size
-    Y = np.empty((k, nidx), dtype=np.float64)
-    rc = lib().orc_apply_left(int(seed), int(dist), int(prec), int(k), _p(A), m, n, n,
-                              None if idx is None else _p(idx), nidx, _p(Y), max(nidx, 1),
-                              int(nthreads or os.cpu_count() or 1))
+    row0, nrows = (0, k) if rows is None else (int(rows[0]), int(rows[1]))
+    Y = np.empty((nrows, nidx), dtype=np.float64)
+    rc = lib().orc_apply_left_rows(int(seed), int(dist), int(prec), int(k), row0, nrows, _p(A),
+                                   m, n, n, None if idx is None else _p(idx), nidx, _p(Y),
+                                   max(nidx, 1), int(nthreads or os.cpu_count() or 1))
     if rc != 0:
         raise ValueError("orc_apply_left failed")
     return Y

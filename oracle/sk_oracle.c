@@ -399,17 +399,49 @@ static int run_jobs(job_t* base, int64_t total, int nthreads, void* (*fn)(void*)
   return rc;
 }
 
+/* Left sketch, rows row0 .. row0+rows-1 of Y = S[k x m] A[m x n], columns idx
+ * (idx == NULL: all n columns, nidx == n), into Y[rows x nidx] (leading dim
+ * ldy).  Row i of the result uses the generated row row0 + i.  Returns 0 or -1. */
+int orc_apply_left_rows(uint64_t seed, int dist, int prec, int64_t k, int64_t row0, int64_t rows,
+                        const float* A, int64_t m, int64_t n, int64_t lda, const int64_t* idx,
+                        int64_t nidx, double* Y, int64_t ldy, int nthreads) {
+  if (k <= 0 || m <= 0 || n <= 0 || lda < n || nidx < 0 || ldy < nidx) return -1;
+  if (row0 < 0 || rows < 0 || row0 + rows > k) return -1;
+  if (!idx && nidx != n) return -1;
+  job_t J = {0};
+  J.seed = seed; J.dist = dist; J.prec = prec; J.k = k;
+  J.A = A; J.m = m; J.n = n; J.lda = lda; J.idx = idx; J.nidx = nidx;
+  J.Y = Y - row0 * ldy; J.ldy = ldy;  /* worker writes row i at Y + i*ldy */
+  job_t* base = &J;
+  if (rows == 0) return 0;
+  /* split [row0, row0+rows) across threads */
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > rows) nthreads = (int)rows;
+  job_t* jobs = (job_t*)calloc((size_t)nthreads, sizeof(job_t));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  if (!jobs || !th) { free(jobs); free(th); return -1; }
+  int rc = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t] = *base;
+    jobs[t].i_begin = row0 + rows * t / nthreads;
+    jobs[t].i_end = row0 + rows * (t + 1) / nthreads;
+    jobs[t].status = -1;
+    if (pthread_create(&th[t], NULL, left_worker, &jobs[t]) != 0) { left_worker(&jobs[t]); th[t] = 0; }
+  }
+  for (int t = 0; t < nthreads; ++t) {
+    if (th[t]) pthread_join(th[t], NULL);
+    if (jobs[t].status != 0) rc = -1;
+  }
+  free(jobs); free(th);
+  return rc;
+}
+
 /* Left sketch: Y[k x nidx] (leading dim ldy) = columns idx of S[k x m] A[m x n].
  * idx == NULL means all n columns (nidx must equal n).  Returns 0 or -1. */
 int orc_apply_left(uint64_t seed, int dist, int prec, int64_t k, const float* A, int64_t m,
                    int64_t n, int64_t lda, const int64_t* idx, int64_t nidx, double* Y,
                    int64_t ldy, int nthreads) {
-  if (k <= 0 || m <= 0 || n <= 0 || lda < n || nidx < 0 || ldy < nidx) return -1;
-  if (!idx && nidx != n) return -1;
-  job_t J = {0};
-  J.seed = seed; J.dist = dist; J.prec = prec; J.k = k;
-  J.A = A; J.m = m; J.n = n; J.lda = lda; J.idx = idx; J.nidx = nidx; J.Y = Y; J.ldy = ldy;
-  return run_jobs(&J, k, nthreads, left_worker);
+  return orc_apply_left_rows(seed, dist, prec, k, 0, k, A, m, n, lda, idx, nidx, Y, ldy, nthreads);
 }
 
 /* Right sketch: Y[nidx x k] (leading dim ldy) = rows idx of A[m x n] S^T, S[k x n].

@@ -1,0 +1,197 @@
+"""ctypes binding of ``libsketch.so`` (the C ABI in include/sketch.h).
+
+Argument marshalling only: every step of the sketch runs in the library's
+CUDA kernels.  The functions keep the C names; tensors may be passed where
+the C ABI takes pointers (their ``data_ptr()`` is used) and a torch stream
+where it takes a ``cudaStream_t``.  The library is loaded on first use; if
+it is missing or stale every call raises ImportError -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsketch.so")
+
+SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT, SK_EBUDGET, SK_EUNSUPPORTED, SK_EBUSY, \
+    SK_ECANCELLED = range(9)
+SK_GAUSSIAN, SK_RADEMACHER, SK_UNIFORM = 0, 1, 2
+SK_FP32, SK_BF16X2, SK_FP8E4M3 = 0, 1, 2
+
+# C prototypes: name -> (restype, argtypes)
+_i64, _u64, _int, _vp, _sz = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, \
+    ctypes.c_size_t
+_P = ctypes.POINTER
+PROTOTYPES = {
+    "sk_create": (_int, [_u64, _int, _i64, _P(_vp)]),
+    "sk_set_precision": (_int, [_vp, _int]),
+    "sk_get_info": (_int, [_vp, _P(_u64), _P(_int), _P(_i64), _P(_int), _P(ctypes.c_float)]),
+    "sk_apply_left": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "sk_apply_right": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "sk_apply_left_host": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "sk_apply_right_host": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "sk_materialize": (_int, [_vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _i64, _vp]),
+    "sk_workspace_size": (_int, [_vp, _int, _i64, _i64, _P(_sz)]),
+    "sk_set_workspace": (_int, [_vp, _vp, _sz]),
+    "sk_stream_status": (_int, [_vp, _vp]),
+    "sk_destroy": (_int, [_vp]),
+    "sk_profile_events": (_int, [_vp, _vp, _vp]),
+    "sk_launch_count": (ctypes.c_uint64, []),
+    "sk_status_string": (ctypes.c_char_p, [_int]),
+    "sk_version": (_int, []),
+}
+
+
+class SketchError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {status_string(status)}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2603_20966_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in PROTOTYPES.items():
+        try:
+            f = getattr(lib, name)
+        except AttributeError as e:
+            raise ImportError(f"{LIB_PATH} lacks {name}: rebuild it") from e
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+class _Lazy:
+    """Loads libsketch.so on first attribute access."""
+    _lib = None
+
+    def __getattr__(self, name):
+        if _Lazy._lib is None:
+            _Lazy._lib = _load()
+        return getattr(_Lazy._lib, name)
+
+
+_lib = _Lazy()
+
+
+def lib():
+    if _Lazy._lib is None:
+        _Lazy._lib = _load()
+    return _Lazy._lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _check(fn, st):
+    if st != SK_OK:
+        raise SketchError(fn, st)
+
+
+def status_string(status: int) -> str:
+    return _lib.sk_status_string(int(status)).decode()
+
+
+def sk_version() -> int:
+    return _lib.sk_version()
+
+
+def sk_create(seed: int, dist: int, k: int) -> int:
+    h = ctypes.c_void_p()
+    _check("sk_create", _lib.sk_create(int(seed) & (2**64 - 1), int(dist), int(k),
+                                       ctypes.byref(h)))
+    return h.value
+
+
+def sk_set_precision(h: int, precision: int) -> None:
+    _check("sk_set_precision", _lib.sk_set_precision(h, int(precision)))
+
+
+def sk_get_info(h: int) -> dict:
+    seed, dist, k, prec, scale = (ctypes.c_uint64(), ctypes.c_int(), ctypes.c_int64(),
+                                  ctypes.c_int(), ctypes.c_float())
+    _check("sk_get_info", _lib.sk_get_info(h, ctypes.byref(seed), ctypes.byref(dist),
+                                           ctypes.byref(k), ctypes.byref(prec),
+                                           ctypes.byref(scale)))
+    return {"seed": seed.value, "dist": dist.value, "k": k.value, "precision": prec.value,
+            "scale": scale.value}
+
+
+def _apply(fn, h, A, m, n, lda, Y, ldy, stream):
+    _check(fn, getattr(_lib, fn)(h, _ptr(A), int(m), int(n), int(lda), _ptr(Y), int(ldy),
+                                 _stream(stream)))
+
+
+def sk_apply_left(h, A, m, n, lda, Y, ldy, stream=None):
+    _apply("sk_apply_left", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_apply_right(h, A, m, n, lda, Y, ldy, stream=None):
+    _apply("sk_apply_right", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_apply_left_host(h, A, m, n, lda, Y, ldy, stream=None):
+    _apply("sk_apply_left_host", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_apply_right_host(h, A, m, n, lda, Y, ldy, stream=None):
+    _apply("sk_apply_right_host", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_materialize(h, row0, col0, rows, cols, fmt, scaled, out, ld, stream=None):
+    _check("sk_materialize", _lib.sk_materialize(h, int(row0), int(col0), int(rows), int(cols),
+                                                 int(fmt), int(scaled), _ptr(out), int(ld),
+                                                 _stream(stream)))
+
+
+def sk_workspace_size(h, side, m, n) -> int:
+    b = ctypes.c_size_t()
+    _check("sk_workspace_size", _lib.sk_workspace_size(h, int(side), int(m), int(n),
+                                                       ctypes.byref(b)))
+    return b.value
+
+
+def sk_set_workspace(h, ptr, nbytes):
+    _check("sk_set_workspace", _lib.sk_set_workspace(h, _ptr(ptr), int(nbytes)))
+
+
+def sk_stream_status(h, stream=None) -> int:
+    return _lib.sk_stream_status(h, _stream(stream))
+
+
+def sk_profile_events(h, start_event, stop_event) -> None:
+    """start_event/stop_event: torch.cuda.Event (or raw cudaEvent_t ints), or None."""
+    def ev(e):
+        if e is None or isinstance(e, int):
+            return e
+        return e.cuda_event
+    _check("sk_profile_events", _lib.sk_profile_events(h, ev(start_event), ev(stop_event)))
+
+
+def sk_launch_count() -> int:
+    return int(_lib.sk_launch_count())
+
+
+def sk_destroy(h) -> None:
+    _check("sk_destroy", _lib.sk_destroy(h))

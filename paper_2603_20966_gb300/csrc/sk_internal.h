@@ -1,0 +1,63 @@
+// sk_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sketch.h"
+
+struct sk_sketch {
+  uint64_t seed;
+  int dist;
+  int64_t k;
+  int prec;
+  float scale;          // fl32(1/sqrt(k))
+  int device;
+  int* d_status;        // device status word (sk_status values), 0 = OK
+  void* ws;             // split-K partials (owned or lent)
+  size_t ws_bytes;
+  bool ws_owned;
+  float* stage_A;       // device staging for the _host entry points
+  size_t stage_A_bytes;
+  float* stage_Y;
+  size_t stage_Y_bytes;
+  cudaEvent_t prof_start;  // optional measurement hook (caller-owned events)
+  cudaEvent_t prof_stop;
+};
+
+namespace sk {
+
+// Count one kernel launch (sk_launch_count).
+void count_launches(uint64_t n);
+
+// Record the handle's measurement-hook event, if any, on `st`.
+inline void prof_mark(cudaEvent_t ev, cudaStream_t st) {
+  if (ev) cudaEventRecord(ev, st);
+}
+
+// Problem of one fused launch: D[P x Q] = sum_l X(p, l) W(l, q) with one
+// operand generated.  LEFT: X = g (P = k), W = A (Q = n), L = m.
+// RIGHT: X = A (P = m), W = g^T (Q = k), L = n.
+struct GemmShape {
+  bool left;
+  int64_t P, Q, L;
+};
+
+// ---- FP32 SIMT form (sk_simt.cu) ----
+size_t simt_workspace_bytes(const GemmShape& s);
+cudaError_t simt_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                        float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t materialize(const sk_sketch* h, int64_t row0, int64_t col0, int64_t rows,
+                        int64_t cols, int fmt, int scaled, void* out, int64_t ld,
+                        cudaStream_t st);
+// fixed-order reduction of split partials: Y[p*ldy+q] = scale * sum_z part[z][p][q]
+cudaError_t splitk_reduce(const float* part, int splits, int64_t P, int64_t Q, float scale,
+                          float* Y, int64_t ldy, cudaStream_t st);
+
+// ---- BF16 split-A tensor-core form (sk_tc.cu) ----
+size_t tc_workspace_bytes(const GemmShape& s);
+sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float* Y, int64_t ldy);
+cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                      float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace sk

@@ -1,0 +1,83 @@
+"""Convenience wrapper over the C ABI for torch tensors.
+
+``Sketch(seed, dist, k)`` owns one library handle.  ``left(A)`` /
+``right(A)`` allocate Y with torch on A's device and call the library on
+torch's current stream; nothing is computed in Python.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native as N
+
+
+class Sketch:
+    def __init__(self, seed: int, dist: int, k: int, precision: int = N.SK_FP32):
+        self.handle = N.sk_create(seed, dist, k)
+        self.k = int(k)
+        if precision != N.SK_FP32:
+            N.sk_set_precision(self.handle, precision)
+
+    def close(self):
+        if self.handle:
+            N.sk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def precision(self) -> int:
+        return N.sk_get_info(self.handle)["precision"]
+
+    @precision.setter
+    def precision(self, p: int):
+        N.sk_set_precision(self.handle, p)
+
+    @property
+    def scale(self) -> float:
+        return N.sk_get_info(self.handle)["scale"]
+
+    @staticmethod
+    def _check(A: torch.Tensor):
+        if A.dtype != torch.float32 or not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a CUDA float32 matrix with unit column stride")
+
+    def left(self, A: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check(A)
+        m, n = A.shape
+        Y = out if out is not None else torch.empty((self.k, n), dtype=torch.float32,
+                                                      device=A.device)
+        N.sk_apply_left(self.handle, A, m, n, A.stride(0), Y, Y.stride(0),
+                        torch.cuda.current_stream(A.device))
+        return Y
+
+    def right(self, A: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check(A)
+        m, n = A.shape
+        Y = out if out is not None else torch.empty((m, self.k), dtype=torch.float32,
+                                                      device=A.device)
+        N.sk_apply_right(self.handle, A, m, n, A.stride(0), Y, Y.stride(0),
+                         torch.cuda.current_stream(A.device))
+        return Y
+
+    def materialize(self, row0: int, col0: int, rows: int, cols: int, fmt: int = N.SK_FP32,
+                    scaled: bool = False, device="cuda") -> torch.Tensor:
+        dt = {N.SK_FP32: torch.float32, N.SK_BF16X2: torch.bfloat16,
+              N.SK_FP8E4M3: torch.uint8}[fmt]
+        out = torch.empty((rows, cols), dtype=dt, device=device)
+        N.sk_materialize(self.handle, row0, col0, rows, cols, fmt, int(scaled), out, cols,
+                         torch.cuda.current_stream(out.device))
+        return out
+
+    def status(self) -> int:
+        return N.sk_stream_status(self.handle, torch.cuda.current_stream())

@@ -1,0 +1,92 @@
+"""Seeded synthetic inputs shaped like the sketching workloads.
+
+This module holds no arithmetic of the sketch itself: it only draws the
+dense input matrices A (with torch's own seeded generators) and describes
+the benchmark configurations.  Tests hand the same tensors to the CUDA path
+and to the CPU oracle.
+
+Workloads (synthetic stand-ins for the paper's metabarcoding and CIFAR-10
+kernel matrices, which are not available):
+  C1  left,  A 4096 x 256 ~ N(0,1), k = 64, Gaussian (seed 7)
+  C2  left,  A 2^20 x 512 ~ N(0,1), k = 2048, Rademacher and Gaussian
+  C3  right, A = U V^T + 1e-3 E, U 65536 x 64, V 16384 x 64, E 65536 x 16384,
+      all N(0,1); Omega 16384 x 256 Gaussian
+  C4  256 independent left sketches, m log-uniform in [1024, 65536],
+      n uniform in [32, 512], k = 2n, alternating distributions
+  C5  Poisson stream of requests drawn like C4 with m up to 2^18
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+A_SEED = 1
+S_SEED = 7
+
+
+def _gen(device, seed: int) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def gaussian_matrix(m: int, n: int, seed: int = A_SEED, device="cpu",
+                    chunk_rows: int = 1 << 16) -> torch.Tensor:
+    """A[m x n] with i.i.d. N(0,1) FP32 entries, drawn in row chunks so that
+    very large matrices never need a second full-size temporary."""
+    out = torch.empty((m, n), dtype=torch.float32, device=device)
+    g = _gen(device, seed)
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        out[r0:r1].normal_(generator=g)
+    return out
+
+
+def lowrank_plus_noise(m: int, n: int, rank: int = 64, noise: float = 1e-3,
+                       seeds=(11, 12, 13), device="cpu", chunk_rows: int = 8192) -> torch.Tensor:
+    """A = U V^T + noise * E with U[m x rank], V[n x rank], E[m x n] ~ N(0,1)."""
+    U = gaussian_matrix(m, rank, seeds[0], device)
+    V = gaussian_matrix(n, rank, seeds[1], device)
+    out = gaussian_matrix(m, n, seeds[2], device)
+    out.mul_(noise)
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        out[r0:r1].addmm_(U[r0:r1], V.t())
+    return out
+
+
+@dataclass(frozen=True)
+class Problem:
+    m: int
+    n: int
+    k: int
+    dist: int
+    seed: int
+
+
+def batched_problems(count: int = 256, m_lo: int = 1024, m_hi: int = 65536, n_lo: int = 32,
+                     n_hi: int = 512, seed: int = 1000) -> list[Problem]:
+    """Independent left-sketch problems: m log-uniform in [m_lo, m_hi],
+    n uniform in [n_lo, n_hi], k = 2n, dist chosen by a per-problem coin,
+    per-problem seeds seed + i."""
+    g = _gen("cpu", seed)
+    u = torch.rand(count, generator=g, dtype=torch.float64)
+    nn = torch.randint(n_lo, n_hi + 1, (count,), generator=g)
+    coin = torch.randint(0, 2, (count,), generator=g)
+    out = []
+    for i in range(count):
+        m = int(round(math.exp(math.log(m_lo) + float(u[i]) * (math.log(m_hi) - math.log(m_lo)))))
+        n = int(nn[i])
+        out.append(Problem(m=m, n=n, k=2 * n, dist=int(coin[i]), seed=seed + i))
+    return out
+
+
+CONFIGS = {
+    "C1": dict(side="left", m=4096, n=256, k=64, dists=(0,), a_seed=A_SEED, s_seed=S_SEED),
+    "C2": dict(side="left", m=1 << 20, n=512, k=2048, dists=(1, 0), a_seed=A_SEED,
+               s_seed=S_SEED),
+    "C3": dict(side="right", m=65536, n=16384, k=256, dists=(0,), a_seed=(11, 12, 13),
+               s_seed=S_SEED),
+}

@@ -107,3 +107,13 @@ def test_expected_gram_is_identity(orc, dist):
 def test_bad_arguments_raise(orc):
     with pytest.raises(ValueError):
         orc.apply_left(1, G, 0, 0, rand_a((4, 4), 0))
+
+
+def test_row_blocks_match_full(orc):
+    A = rand_a((70, 9), 12)
+    full = orc.apply_left(2, G, 0, 20, A)
+    np.testing.assert_array_equal(orc.apply_left(2, G, 0, 20, A, rows=(5, 11)), full[5:16])
+    np.testing.assert_array_equal(orc.apply_left(2, G, 0, 20, A, rows=(19, 1), cols=[3, 1]),
+                                  full[19:20, [3, 1]])
+    with pytest.raises(ValueError):
+        orc.apply_left(2, G, 0, 20, A, rows=(15, 6))
