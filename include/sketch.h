@@ -110,6 +110,30 @@ sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64
 sk_status sk_apply_right(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
                          float* Y, int64_t ldy, void* stream);
 
+/* Left sketch that allocates no device memory, for callers that cannot let
+ * a library call cudaMalloc: an application whose device memory belongs to
+ * another allocator (a framework's caching allocator, a serving engine that
+ * reserves HBM up front), or a latency-critical path that cannot absorb the
+ * implicit synchronisation of cudaMalloc/cudaFree.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Computes the same Y[k x n] = S[k x m] A[m x n] as sk_apply_left in the
+ * FP32 form (the handle's precision must be SK_FP32, else
+ * SK_EUNSUPPORTED), with the same argument meaning and layout.  Its split-K
+ * partials live in a 16 MiB array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  Problems whose
+ * partials would exceed it -- splits * k * n * 4 bytes > 16 MiB, with
+ * sk_workspace_size(h, 0, m, n) reporting that byte count -- are rejected
+ * with SK_EUNSUPPORTED before anything is enqueued.  The first call on each
+ * device looks up that device's address of the array (set-up that
+ * allocates nothing); make that first call before any stream capture.
+ * All calls on a device share the array and each call writes every partial
+ * it later reads, so nothing needs clearing between calls, but calls whose
+ * work overlaps on the GPU (different streams, no ordering) race on it and
+ * give undefined results: order them on one stream or with events. */
+sk_status sk_apply_left_noalloc(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
+                                float* Y, int64_t ldy, void* stream);
+
 /* The same two products with HOST buffers: A is copied to the device, the
  * sketch computed, and Y copied back before the call returns (the call
  * synchronises `stream`).  Pinned host memory gives full copy bandwidth;

@@ -30,6 +30,7 @@ PROTOTYPES = {
     "sk_get_info": (_int, [_vp, _P(_u64), _P(_int), _P(_i64), _P(_int), _P(ctypes.c_float)]),
     "sk_apply_left": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_apply_right": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "sk_apply_left_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_apply_left_host": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_apply_right_host": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_materialize": (_int, [_vp, _i64, _i64, _i64, _i64, _int, _int, _vp, _i64, _vp]),
@@ -149,6 +150,12 @@ def sk_apply_left(h, A, m, n, lda, Y, ldy, stream=None):
 
 def sk_apply_right(h, A, m, n, lda, Y, ldy, stream=None):
     _apply("sk_apply_right", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_apply_left_noalloc(h, A, m, n, lda, Y, ldy, stream=None):
+    """FP32 left sketch whose scratch is a fixed array inside the library:
+    for callers that must not have this library allocate device memory."""
+    _apply("sk_apply_left_noalloc", h, A, m, n, lda, Y, ldy, stream)
 
 
 def sk_apply_left_host(h, A, m, n, lda, Y, ldy, stream=None):

@@ -278,3 +278,73 @@ cudaError_t materialize(const sk_sketch* h, int64_t row0, int64_t col0, int64_t 
 }
 
 }  // namespace sk
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP32 left sketch.
+//
+// Some callers cannot let this library call cudaMalloc: applications whose
+// device memory is owned by another allocator (a framework's caching
+// allocator or a serving engine that reserves HBM up front and accounts for
+// every byte), and latency-critical paths that cannot afford the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree.  For them the split-K
+// partials of the FP32 left sketch live in a fixed array compiled into the
+// library instead of in an allocated workspace.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace sk {
+namespace {
+
+// 16 MiB of FP32 split-K partials.  Every GPU that loads this library holds
+// this array until the process exits; all calls on a device share it.
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) float g_static_scratch[kStaticScratchBytes / sizeof(float)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_scratch_mu;
+void* g_static_scratch_addr[kMaxDevices];
+
+// Device address of g_static_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+  if (g_static_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_scratch_addr[dev] = p;
+  }
+  *out = g_static_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace sk
+
+extern "C" sk_status sk_apply_left_noalloc(sk_handle h, const float* A, int64_t m, int64_t n,
+                                           int64_t lda, float* Y, int64_t ldy, void* stream) {
+  if (!h || !A || !Y || m <= 0 || n <= 0 || lda < n || ldy < n || m >= 4294967296LL)
+    return SK_EINVAL;
+  if (h->prec != SK_FP32) return SK_EUNSUPPORTED;
+  sk::GemmShape s;
+  s.left = true;
+  s.P = h->k;
+  s.Q = n;
+  s.L = m;
+  if (sk::simt_workspace_bytes(s) > sk::kStaticScratchBytes) return SK_EUNSUPPORTED;
+  void* scratch = nullptr;
+  cudaError_t e = sk::static_scratch_address(&scratch);
+  if (e == cudaSuccess)
+    e = sk::simt_sketch(h, s, A, lda, Y, ldy, scratch, sk::kStaticScratchBytes,
+                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SK_ECUDA;
+  }
+  return SK_OK;
+}
