@@ -1,0 +1,130 @@
+"""GPU parity of the BF16 split-A tensor-core form (sk_set_precision(SK_BF16X2),
+tcgen05 + TMEM + TMA) against the FP64 CPU oracle of the product with
+S = bf16(g): relative Frobenius error <= 1e-5 at ragged shapes spanning
+several tiles, splits and a ragged tail, and on sampled entries at the full
+2^20 x 512, k = 2048 workload in the launch configuration bench.py times."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import rel_frob, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+G, R, U = 0, 1, 2
+BF16 = 1
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    require_gpu()
+    import paper_2603_20966_gb300 as P
+    return P
+
+
+def _A(m, n, seed, device="cpu"):
+    from paper_2603_20966_gb300.workloads import gaussian_matrix
+    return gaussian_matrix(m, n, seed, device=device)
+
+
+def run_left(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
+    m, n = A.shape
+    lda = lda or (n + 3) // 4 * 4
+    ldy = ldy or (n + 3) // 4 * 4
+    Ad = torch.zeros((m, lda), dtype=torch.float32, device="cuda")
+    Ad[:, :n] = A.cuda()
+    Y = torch.full((k, ldy), float("nan"), dtype=torch.float32, device="cuda")
+    h = P.sk_create(seed, dist, k)
+    try:
+        P.sk_set_precision(h, prec)
+        P.sk_apply_left(h, Ad, m, n, lda, Y, ldy)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    return Y[:, :n].cpu().numpy()
+
+
+SHAPES = [(128, 4096, 512), (64, 4096, 256), (100, 1000, 48), (130, 777, 300), (1, 16, 16),
+          (3, 5, 7), (256, 70000, 1000), (2048, 65536, 512), (200, 300000, 20)]
+
+
+@pytest.mark.parametrize("dist", [R, G])
+@pytest.mark.parametrize("k,m,n", SHAPES)
+def test_left_bf16x2_matches_oracle(P, orc, dist, k, m, n):
+    A = _A(m, n, 31 * k + m + n)
+    got = run_left(P, 7, dist, k, A)
+    assert np.all(np.isfinite(got))
+    ref = orc.apply_left(7, dist, BF16, k, A.numpy())
+    err = rel_frob(got, ref)
+    assert err <= TOL, err
+
+
+def test_left_bf16x2_uniform(P, orc):
+    A = _A(3000, 64, 5)
+    got = run_left(P, 11, U, 96, A)
+    assert rel_frob(got, orc.apply_left(11, U, BF16, 96, A.numpy())) <= TOL
+
+
+@pytest.mark.parametrize("dist", [R, G])
+def test_identity_gives_scaled_bf16_matrix_exactly(P, orc, dist):
+    m, k = 512, 200
+    got = run_left(P, 13, dist, k, torch.eye(m))
+    ref = orc.generate(13, dist, BF16, 0, 0, k, m) * orc.scale(k)  # fl32(s * bf16(g))
+    np.testing.assert_array_equal(got, ref.astype(np.float32))
+
+
+def test_rademacher_bf16x2_agrees_with_fp32_form(P):
+    # S is exactly +-1 in both forms, so both approximate the same exact product;
+    # each is within TOL of it, hence within 2*TOL of each other
+    A = _A(100000, 512, 3)
+    a = run_left(P, 5, R, 512, A, prec=BF16)
+    b = run_left(P, 5, R, 512, A, prec=0)
+    assert rel_frob(a, b) <= 2 * TOL
+
+
+def test_deterministic(P):
+    A = _A(50000, 300, 4)
+    a = run_left(P, 2, G, 256, A)
+    b = run_left(P, 2, G, 256, A)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_leading_dimensions_and_alignment(P, orc):
+    A = _A(2000, 100, 6)
+    got = run_left(P, 3, G, 64, A, lda=128, ldy=104)
+    assert rel_frob(got, orc.apply_left(3, G, BF16, 64, A.numpy())) <= TOL
+    h = P.sk_create(3, G, 64)
+    Ad = torch.zeros((2000, 101), device="cuda")
+    Y = torch.zeros((64, 104), device="cuda")
+    try:
+        P.sk_set_precision(h, BF16)
+        with pytest.raises(P.SketchError):  # lda not a multiple of 4 (TMA row pitch)
+            P.sk_apply_left(h, Ad, 2000, 100, 101, Y, 104)
+        with pytest.raises(P.SketchError):  # misaligned base pointer
+            P.sk_apply_left(h, Ad.data_ptr() + 4, 2000, 100, 104, Y, 104)
+    finally:
+        P.sk_destroy(h)
+
+
+@pytest.mark.parametrize("dist", [R, G])
+def test_full_size_tall_skinny_sampled(P, orc, dist):
+    # the 2^20 x 512, k = 2048 workload exactly as bench.py launches it
+    m, n, k = 1 << 20, 512, 2048
+    A = _A(m, n, 1, device="cuda")
+    Y = torch.empty((k, n), device="cuda")
+    h = P.sk_create(7, dist, k)
+    try:
+        P.sk_set_precision(h, BF16)
+        P.sk_apply_left(h, A, m, n, n, Y, n)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    cols = np.array([0, 1, 255, 256, 511])
+    a_cols = A[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    rows = (1000, 96)
+    ref = orc.apply_left(7, dist, BF16, k, a_cols, rows=rows)
+    got = Y[rows[0]:rows[0] + rows[1]][:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    err = rel_frob(got, ref)
+    assert err <= TOL, err
+    assert torch.isfinite(Y).all()
