@@ -168,6 +168,17 @@ sk_status sk_set_workspace(sk_handle h, void* ptr, size_t bytes);
  * call are undefined), or SK_ECUDA if the stream reported an error. */
 sk_status sk_stream_status(sk_handle h, void* stream);
 
+/* Synchronise `stream` and copy the handle's four device status words
+ * without clearing them: [0] the sk_status sk_stream_status would return,
+ * [1] where the first bounded wait that gave up was waiting (role * 16 +
+ * barrier: roles 1 TMA producer, 2 MMA issuer, 3 epilogue, 4 worker,
+ * 5 relay; barriers 0 staging full, 1 staging empty, 2 operand full,
+ * 3 operand empty, 4 accumulator full, 5 accumulator empty, 6 MMA stage
+ * done), [2] the pipeline stage (or
+ * accumulation chain) it was waiting for, [3] the linear index of its CTA.
+ * Words 1-3 are meaningful only when word 0 is SK_ETIMEOUT. */
+sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]);
+
 /* Release the handle and the device memory it owns.  Waits for nothing:
  * the caller must ensure no enqueued work still uses it. */
 sk_status sk_destroy(sk_handle h);
@@ -186,6 +197,10 @@ uint64_t sk_launch_count(void);
 
 /* Static human-readable name of a status code. */
 const char* sk_status_string(int status);
+
+/* Description of the CUDA error behind the most recent SK_ECUDA / SK_ENOMEM
+ * returned to the calling host thread ("no error" if none). */
+const char* sk_last_cuda_error(void);
 
 /* Library version as an integer MAJOR*10000 + MINOR*100 + PATCH. */
 int sk_version(void);

@@ -37,10 +37,12 @@ PROTOTYPES = {
     "sk_workspace_size": (_int, [_vp, _int, _i64, _i64, _P(_sz)]),
     "sk_set_workspace": (_int, [_vp, _vp, _sz]),
     "sk_stream_status": (_int, [_vp, _vp]),
+    "sk_debug_status": (_int, [_vp, _vp, _P(ctypes.c_int32)]),
     "sk_destroy": (_int, [_vp]),
     "sk_profile_events": (_int, [_vp, _vp, _vp]),
     "sk_launch_count": (ctypes.c_uint64, []),
     "sk_status_string": (ctypes.c_char_p, [_int]),
+    "sk_last_cuda_error": (ctypes.c_char_p, []),
     "sk_version": (_int, []),
 }
 
@@ -48,7 +50,10 @@ PROTOTYPES = {
 class SketchError(RuntimeError):
     def __init__(self, fn: str, status: int):
         self.status = status
-        super().__init__(f"{fn}: {status_string(status)}")
+        detail = ""
+        if status in (SK_ECUDA, SK_ENOMEM):
+            detail = f" ({_lib.sk_last_cuda_error().decode()})"
+        super().__init__(f"{fn}: {status_string(status)}{detail}")
 
 
 def _load():
@@ -198,6 +203,13 @@ def sk_profile_events(h, start_event, stop_event) -> None:
 
 def sk_launch_count() -> int:
     return int(_lib.sk_launch_count())
+
+
+def sk_debug_status(h, stream=None) -> list[int]:
+    """The four device status words (status, wait site, stage, CTA); see sketch.h."""
+    out = (ctypes.c_int32 * 4)()
+    _check("sk_debug_status", _lib.sk_debug_status(h, _stream(stream), out))
+    return list(out)
 
 
 def sk_destroy(h) -> None:

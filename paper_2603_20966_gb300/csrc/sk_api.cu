@@ -21,8 +21,11 @@ namespace {
 
 constexpr int64_t kMaxIndex = 4294967296LL;  // generator indices are 32-bit
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 sk_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return SK_OK;
+  g_last_cuda_error = e;
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
 }
@@ -236,10 +239,17 @@ sk_status sk_stream_status(sk_handle h, void* stream) {
   e = cudaMemcpy(&word, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return from_cuda(e);
   if (word != 0) {
-    e = cudaMemset(h->d_status, 0, sizeof(int));
+    e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
     if (e != cudaSuccess) return from_cuda(e);
   }
   return static_cast<sk_status>(word);
+}
+
+sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]) {
+  if (!h || !out) return SK_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaMemcpy(out, h->d_status, sizeof(int) * 4, cudaMemcpyDeviceToHost);
+  return from_cuda(e);
 }
 
 sk_status sk_destroy(sk_handle h) {
@@ -274,6 +284,10 @@ const char* sk_status_string(int status) {
     case SK_ECANCELLED: return "SK_ECANCELLED: request cancelled";
     default: return "unknown sk_status";
   }
+}
+
+const char* sk_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no error" : cudaGetErrorString(g_last_cuda_error);
 }
 
 int sk_version(void) { return 100; }

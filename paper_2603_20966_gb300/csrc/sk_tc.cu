@@ -1,33 +1,43 @@
 // sk_tc.cu -- BF16 split-A tensor-core form of the fused generate-and-sketch
-// on Blackwell (tcgen05 + TMEM + TMA), left sketch Y[k x n] = S[k x m] A[m x n].
+// on Blackwell (tcgen05 + TMEM + TMA, CTA pairs), left sketch
+// Y[k x n] = S[k x m] A[m x n].
 //
 // This is the local multiply of the paper's Alg. 1 (GenRandom, then
 // B = A Omega on the local block) with the random operand regenerated inside
 // the kernel instead of read (Sec. 6.2's "generate rather than communicate",
 // with shared memory in the role of the processor's local memory).
 //
-// One CTA per SM owns a 128 x NT tile of Y (NT <= 512 TMEM columns) and one
-// contiguous range of the contracted dimension m (deterministic split-K):
-//   warp 0       TMA producer: FP32 A tiles [16 rows of m x NT cols] into a
-//                3-stage staging ring (zero fill beyond the matrix);
-//   warp 1       TMEM allocator and MMA issuer: per stage 2 passes (hi, lo) x
-//                NT/256 tcgen05.mma kind::f16 (M=128, K=16) into one FP32
-//                accumulator in TMEM;
-//   warps 2-5    epilogue: every CHAIN stages the accumulator is read out of
-//                TMEM (tcgen05.ld) and added into the CTA's FP32 partial in
-//                global memory (store for the first chain, red.add after);
-//   warps 6-21   workers: each stage, every worker generates its share of the
-//                BF16 S tile [128 x 16] (Philox4x32-10 + Box-Muller or sign
-//                bits) and converts its share of the FP32 staging tile into
-//                BF16 hi = bf16(a), lo = bf16(a - hi), both in the K-major
-//                no-swizzle operand layout.
+// Shared-memory bandwidth, not the tensor core, bounds this product: every
+// stage the MMA re-reads its operands from shared memory while the FP32 A
+// tile is written by TMA, read back and written again as BF16 hi / lo.  A CTA
+// pair (cta_group::2) halves that traffic per SM: one MMA of M = 256 spans
+// both SMs, each CTA supplying 128 rows of S and half of the B (= A tile)
+// rows, so each CTA loads and converts only half of every A tile.
+//
+// A pair owns a 256 x NT tile of Y (NT <= 512 TMEM columns in each CTA) and
+// one contiguous range of the contracted dimension m (deterministic split-K):
+//   warp 0       TMA producer: this CTA's FP32 columns of each A tile
+//                [16 rows of m] into a staging ring;
+//   warp 1       TMEM allocation (collective over the pair); in the even CTA
+//                the MMA issuer: per stage 2 passes (hi, lo) x NT/256
+//                tcgen05.mma kind::f16 (M=256, K=16) into the FP32 accumulator;
+//   warp 2       relay (even CTA): forwards each stage's and each chain's
+//                completion to the odd CTA;
+//   warps 3-10   epilogue: every CHAIN stages the accumulator is read out of
+//                this CTA's TMEM and added into its FP32 partial in global
+//                memory (store for the first chain, red.add after);
+//   warps 11-26  workers: each stage, generate this CTA's BF16 S tile
+//                [128 x 16] (Philox4x32-10 + Box-Muller, or sign bits) and
+//                convert its A columns into hi = bf16(a), lo = bf16(a - hi) in
+//                the K-major no-swizzle operand layout.
+// With k <= 128 a single CTA (cta_group::1, M = 128) does the same alone.
 // The tensor core accumulates in FP32 without round-to-nearest on every
 // add, so its error grows with the chain length; restarting the TMEM chain
 // every CHAIN stages and summing chains with IEEE adds keeps Y within 1e-5
 // of the exact product at any m.  S never exists outside shared memory.
-// Every wait is bounded: on timeout the kernel records SK_ETIMEOUT in the
-// handle's status word, drains its own copies and MMAs (again bounded) and
-// frees TMEM before returning.
+// Every wait is bounded: on timeout the kernel records SK_ETIMEOUT and the
+// waiting site in the handle's status words, drains its own copies and MMAs
+// (again bounded) and frees TMEM; both CTAs reach the closing cluster barrier.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -42,33 +52,39 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128;       // generated rows per CTA (MMA M)
+constexpr int BM = 128;       // generated rows per CTA
 constexpr int BK = 16;        // contracted length per stage (MMA K)
-constexpr int NT_MAX = 512;   // output columns per CTA (TMEM columns)
-constexpr int NSF = 3;        // FP32 staging stages
-constexpr int NSO = 3;        // operand stages
-constexpr int CHAIN = 64;     // stages per TMEM accumulation chain
-constexpr int NUM_EPI_WARPS = 4;
+constexpr int NT_MAX = 512;   // output columns per tile (TMEM columns)
+constexpr int CHAIN = 128;    // stages per TMEM accumulation chain
+constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_WORK_WARPS = 16;
 constexpr int WARP_TMA = 0;
 constexpr int WARP_MMA = 1;
-constexpr int WARP_EPI0 = 2;
+constexpr int WARP_RELAY = 2;
+constexpr int WARP_EPI0 = 3;
 constexpr int WARP_WORK0 = WARP_EPI0 + NUM_EPI_WARPS;
-constexpr int NWORK = 32 * NUM_WORK_WARPS;                   // 512 worker threads
-constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 704
+constexpr int NWORK = 32 * NUM_WORK_WARPS;
+constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 864
 
-constexpr uint32_t STAGE_F_BYTES = BK * NT_MAX * 4;  // 32 KB
-constexpr uint32_t OPB_BYTES = NT_MAX * BK * 2;      // 16 KB (hi or lo)
-constexpr uint32_t OPS_BYTES = BM * BK * 2;          // 4 KB
-constexpr uint32_t OFF_F = 0;
-constexpr uint32_t OFF_BHI = OFF_F + NSF * STAGE_F_BYTES;
-constexpr uint32_t OFF_BLO = OFF_BHI + NSO * OPB_BYTES;
-constexpr uint32_t OFF_S = OFF_BLO + NSO * OPB_BYTES;
-constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS_BYTES;
-constexpr uint32_t NUM_BARS = 2 * NSF + 2 * NSO + 3;
-constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
-constexpr uint32_t SMEM_BYTES = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+// Per-CTA buffers.  A CTA of a pair holds NT/2 columns of each A tile.
+template <bool PAIR>
+struct Cfg {
+  static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // A columns per CTA
+  static constexpr int NSF = PAIR ? 5 : 3;                  // FP32 staging stages
+  static constexpr int NSO = PAIR ? 5 : 3;                  // operand stages
+  static constexpr uint32_t STAGE_F = BK * COLS * 4;        // FP32 staging
+  static constexpr uint32_t OPB = COLS * BK * 2;            // hi or lo operand
+  static constexpr uint32_t OPS = BM * BK * 2;              // S tile
+  static constexpr uint32_t OFF_F = 0;
+  static constexpr uint32_t OFF_BHI = OFF_F + NSF * STAGE_F;
+  static constexpr uint32_t OFF_BLO = OFF_BHI + NSO * OPB;
+  static constexpr uint32_t OFF_S = OFF_BLO + NSO * OPB;
+  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
+  static constexpr uint32_t NUM_BARS = 2 * NSF + 3 * NSO + 3;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
+  static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
 
 // K-major no-swizzle operand layout (16-element K slab): core matrix
 // (8 rows x 16 B) at (row/8)*256 + khalf*128, row r%8 at +16*(r%8).
@@ -82,9 +98,7 @@ struct TcParams {
   float* part;      // partials [splits][P][Q] (every chain is summed here)
   int64_t P, Q, L;  // P = k, Q = n, L = m
   int64_t chunk;    // contracted length per split (multiple of BK)
-  int nt;           // output columns per CTA: multiple of 16 up to 256, or 512
-  int boxn;         // TMA box width in columns
-  int nbox;         // TMA boxes per stage
+  int nt;           // output columns per tile: multiple of 16 (32 for pairs) up to 256, or 512
   int tmem_cols;    // power of two >= max(32, nt)
   PhiloxKey key;
   int* status;
@@ -105,118 +119,170 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64
   }
 }
 
-template <int DIST>
+template <int DIST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_sketch_bf16x2_left(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
+  using C = Cfg<PAIR>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bar0 = sbase + OFF_BAR;
+  const uint32_t bar0 = sbase + C::OFF_BAR;
   auto full_f = [&](int i) { return bar0 + 8u * i; };
-  auto empty_f = [&](int i) { return bar0 + 8u * (NSF + i); };
-  auto full_o = [&](int i) { return bar0 + 8u * (2 * NSF + i); };
-  auto empty_o = [&](int i) { return bar0 + 8u * (2 * NSF + NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (2 * NSF + 2 * NSO);
+  auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
+  auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
+  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
+  auto mma_done = [&](int i) { return bar0 + 8u * (2 * C::NSF + 2 * C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 3 * C::NSO);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 4);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * p.nt;
-  const int64_t p0 = static_cast<int64_t>(blockIdx.y) * BM;
+  const uint32_t rank = PAIR ? (cluster_ctarank() & 1u) : 0u;  // 0 = even (MMA issuer)
+  const bool leader = rank == 0;
+  const int nt = p.nt;
+  const int nmma = nt > 256 ? 2 : 1;                 // MMA instructions per pass
+  const int nh = nt > 256 ? 256 : nt;                // N of each instruction
+  const int bh = PAIR ? nh / 2 : nh;                 // B rows per instruction in this CTA
+  const int cols = nmma * bh;                        // A columns this CTA loads/converts
+  // grid: x = 128-row tiles of Y (pairs are adjacent in x), y = column tiles
+  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nt;
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * BM;
   const int64_t lbeg = static_cast<int64_t>(blockIdx.z) * p.chunk;
   const int64_t lend = min(p.L, lbeg + p.chunk);
   const int nsteps = static_cast<int>((lend - lbeg + BK - 1) / BK);
   const int nchains = (nsteps + CHAIN - 1) / CHAIN;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSF; ++i) {
+    for (int i = 0; i < C::NSF; ++i) {
       mbar_init(full_f(i), 1);
       mbar_init(empty_f(i), NUM_WORK_WARPS);
     }
-    for (int i = 0; i < NSO; ++i) {
-      mbar_init(full_o(i), NUM_WORK_WARPS);
+    for (int i = 0; i < C::NSO; ++i) {
+      mbar_init(full_o(i), NUM_WORK_WARPS * (PAIR ? 2 : 1));  // workers of both CTAs
       mbar_init(empty_o(i), 1);
+      mbar_init(mma_done(i), 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, NUM_EPI_WARPS);
+    mbar_init(acc_empty, NUM_EPI_WARPS * (PAIR ? 2 : 1));  // epilogues of both CTAs
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     mbar_fence_init();
   }
   if (warp == WARP_MMA) {
-    tmem_alloc(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+      tmem_relinquish();
+    }
   }
   if (warp == WARP_TMA && lane == 0) tma_prefetch_desc(&tmapA);
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's barriers exist before any remote arrive
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const Abort ab{abort_flag, p.status, p.timeout_ns};
+  // barriers of the even CTA, addressed from either CTA
+  const uint32_t lead_full_o = PAIR ? mapa_shared(full_o(0), 0u) : full_o(0);
+  const uint32_t lead_acc_empty = PAIR ? mapa_shared(acc_empty, 0u) : acc_empty;
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
-      const uint32_t tx = static_cast<uint32_t>(p.nbox * p.boxn * BK * 4);
+      const uint32_t tx = static_cast<uint32_t>(cols * BK * 4);
       int issued = 0;
       for (int s = 0; s < nsteps; ++s) {
-        const int sf = s % NSF;
-        if (s >= NSF && !mbar_wait(empty_f(sf), ((s / NSF) & 1) ^ 1, ab)) break;
+        const int sf = s % C::NSF;
+        if (s >= C::NSF && !mbar_wait(empty_f(sf), ((s / C::NSF) & 1) ^ 1, ab, 0x11, s)) break;
         mbar_arrive_expect_tx(full_f(sf), tx);
         const int32_t y = static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK);
-        const uint32_t dst = sbase + OFF_F + sf * STAGE_F_BYTES;
-        for (int b = 0; b < p.nbox; ++b)
-          tma_load_2d(dst + static_cast<uint32_t>(b * p.boxn * BK * 4), &tmapA,
-                      static_cast<int32_t>(q0 + b * p.boxn), y, full_f(sf));
+        for (int h = 0; h < nmma; ++h)
+          tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(h * bh * BK * 4),
+                      &tmapA, static_cast<int32_t>(q0 + h * 256 + static_cast<int>(rank) * bh), y,
+                      full_f(sf));
         issued = s + 1;
       }
       if (*abort_flag) {  // let the copies already issued land before leaving
-        for (int s = max(0, issued - NSF); s < issued; ++s)
-          drain_wait(full_f(s % NSF), (s / NSF) & 1, 100000000ull);
+        for (int s = max(0, issued - C::NSF); s < issued; ++s)
+          drain_wait(full_f(s % C::NSF), (s / C::NSF) & 1, 100000000ull);
       }
     }
   } else if (warp == WARP_MMA) {
-    if (lane == 0) {
-      const int nmma = p.nt > 256 ? 2 : 1;
-      const uint32_t idesc = idesc_bf16_f32(128, static_cast<uint32_t>(p.nt > 256 ? 256 : p.nt));
+    if (lane == 0 && leader) {
+      const uint32_t idesc =
+          idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(nh));
       for (int s = 0; s < nsteps; ++s) {
-        const int so = s % NSO;
+        const int so = s % C::NSO;
         const int in_chain = s % CHAIN;
-        // a new chain may start only after the epilogue has read the last one
-        if (s > 0 && in_chain == 0 && !mbar_wait(acc_empty, ((s / CHAIN) - 1) & 1, ab)) break;
-        if (!mbar_wait(full_o(so), (s / NSO) & 1, ab)) break;
+        // a new chain may start only after every epilogue has read the last one
+        if (s > 0 && in_chain == 0 &&
+            !mbar_wait(acc_empty, ((s / CHAIN) - 1) & 1, ab, 0x25, s))
+          break;
+        if (!mbar_wait(full_o(so), (s / C::NSO) & 1, ab, 0x22, s)) break;
         tc_fence_after();
-        const uint64_t adesc = smem_desc(sbase + OFF_S + so * OPS_BYTES, LBO, SBO);
+        const uint64_t adesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
-          const uint32_t bb = sbase + (pass ? OFF_BLO : OFF_BHI) + so * OPB_BYTES;
+          const uint32_t bb = sbase + (pass ? C::OFF_BLO : C::OFF_BHI) + so * C::OPB;
           for (int h = 0; h < nmma; ++h) {
-            const uint64_t bdesc = smem_desc(bb + static_cast<uint32_t>(h) * (256u / 8u) * SBO,
-                                             LBO, SBO);
-            mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc,
-                     (in_chain > 0 || pass > 0) ? 1u : 0u);
+            const uint64_t bdesc =
+                smem_desc(bb + static_cast<uint32_t>(h * bh / 8) * SBO, LBO, SBO);
+            const uint32_t acc = (in_chain > 0 || pass > 0) ? 1u : 0u;
+            if (PAIR)
+              mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+            else
+              mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
           }
         }
-        mma_commit(empty_o(so));
-        if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit(acc_full);
+        const bool chain_end = in_chain == CHAIN - 1 || s == nsteps - 1;
+        if (PAIR) {
+          mma_commit_pair(mma_done(so));  // the relay frees the operands of both CTAs
+          if (chain_end) mma_commit_pair(acc_full);
+        } else {
+          mma_commit(empty_o(so));
+          if (chain_end) mma_commit(acc_full);
+        }
       }
-      mma_commit(drain_bar);  // completes once every MMA issued above has finished
+      if (PAIR)
+        mma_commit_pair(drain_bar);
+      else
+        mma_commit(drain_bar);
+      // every MMA has finished before this CTA reaches the closing barrier
+      drain_wait(drain_bar, 0, 200000000ull);
+    }
+  } else if (warp == WARP_RELAY) {
+    if (PAIR && leader && lane == 0) {
+      const uint32_t peer_empty = mapa_shared(empty_o(0), 1u);
+      const uint32_t peer_acc = mapa_shared(acc_full, 1u);
+      for (int s = 0; s < nsteps; ++s) {
+        const int so = s % C::NSO;
+        if (!mbar_wait(mma_done(so), (s / C::NSO) & 1, ab, 0x56, s)) break;
+        mbar_arrive(empty_o(so));
+        mbar_arrive_cluster(peer_empty + 8u * so);
+        if (s % CHAIN == CHAIN - 1 || s == nsteps - 1) {
+          if (!mbar_wait(acc_full, (s / CHAIN) & 1, ab, 0x54, s)) break;
+          mbar_arrive_cluster(peer_acc);
+        }
+      }
     }
   } else if (warp < WARP_WORK0) {
-    // ---- epilogue: add each finished chain into the CTA's FP32 partial ----
+    // ---- epilogue: add each finished chain into this CTA's FP32 partial ----
     const int quarter = warp & 3;
+    const int colset = (warp - WARP_EPI0) >> 2;  // 0 or 1: even / odd 32-column chunks
     const int row = quarter * 32 + lane;
     const int64_t gp = p0 + row;
     float* dst_row = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gp) * p.Q + q0;
     const bool vec_ok = (p.Q % 4) == 0;
     for (int c = 0; c < nchains; ++c) {
-      const bool ok = mbar_wait(acc_full, c & 1, ab);
+      const bool ok = mbar_wait(acc_full, c & 1, ab, 0x34, c);
       if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld below is warp-collective
       tc_fence_after();
-      for (int ci = 0; ci * 32 < p.nt; ++ci) {
+      for (int ci = colset; ci * 32 < nt; ci += 2) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                       static_cast<uint32_t>(ci * 32),
@@ -249,51 +315,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) {
+        if (PAIR)
+          mbar_arrive_cluster(lead_acc_empty);
+        else
+          mbar_arrive(acc_empty);
+      }
     }
   } else {
-    // ---- workers: generate the S tile and convert the A tile ----
-    const int wt = threadIdx.x - 32 * WARP_WORK0;  // 0..511
-    const int nt = p.nt;
-    const int boxn = p.boxn;
-    // generation task of this thread (fixed across stages)
-    //   Rademacher: row wt%128, k-half wt/128 (threads < 256), 8 entries
-    //   Gaussian / uniform: 8 rows x 4 quads per warp, 4 entries each
-    uint32_t g_row, g_off, g_col;
-    bool g_active;
-    if (DIST == kRademacher) {
-      g_row = static_cast<uint32_t>(wt & (BM - 1));
-      g_col = 8u * static_cast<uint32_t>(wt >> 7);
-      g_off = kmaj_off(g_row, static_cast<uint32_t>(wt >> 7));
-      g_active = wt < 2 * BM;
-    } else {
-      const uint32_t l = static_cast<uint32_t>(wt & 31);
-      g_row = static_cast<uint32_t>(wt >> 5) * 8u + (l >> 2);
-      const uint32_t qd = l & 3u;
-      g_col = 4u * qd;
-      g_off = kmaj_off(g_row, qd >> 1) + (qd & 1u) * 8u;
-      g_active = true;
-    }
-    const int64_t grow = p0 + g_row;
-    const bool row_ok = grow < p.P;
+    // ---- workers: generate this CTA's S tile and convert its A columns ----
+    const int wt = threadIdx.x - 32 * WARP_WORK0;
     uint32_t cached_blk = 0xffffffffu;
     uint4 words = make_uint4(0u, 0u, 0u, 0u);
-
     for (int s = 0; s < nsteps; ++s) {
-      const int sf = s % NSF;
-      const int so = s % NSO;
-      bool ok = s < NSO || mbar_wait(empty_o(so), ((s / NSO) & 1) ^ 1, ab);
+      const int sf = s % C::NSF;
+      const int so = s % C::NSO;
+      // the MMAs that read operand buffer `so` last time have completed
+      bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
       if (!__all_sync(0xffffffffu, ok)) break;  // leave together (abort path)
-      uint8_t* sdst = smem + OFF_S + so * OPS_BYTES;
+      uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
-      if (g_active) {
-        const int64_t c0 = cbase + g_col;
-        if (DIST == kRademacher) {
+      if (DIST == kRademacher) {
+        // 128 rows x 2 k-halves, 8 entries each, one Philox call per 128 columns
+        for (int t = wt; t < 2 * BM; t += NWORK) {
+          const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
+          const uint32_t hh = static_cast<uint32_t>(t >> 7);
+          const int64_t grow = p0 + r;
+          const int64_t c0 = cbase + 8 * hh;
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          if (row_ok && c0 < lend) {
+          if (grow < p.P && c0 < lend) {
             const uint32_t c = static_cast<uint32_t>(c0);
             const uint32_t blk = c >> 7;
-            if (blk != cached_blk) {
+            if (blk != cached_blk) {  // the same thread keeps the same (row, half)
               words = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
               cached_blk = blk;
             }
@@ -307,33 +360,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             v.z = 0x3F803F80u | ((bits & 16u) << 11) | ((bits & 32u) << 26);
             v.w = 0x3F803F80u | ((bits & 64u) << 9) | ((bits & 128u) << 24);
           }
-          *reinterpret_cast<uint4*>(sdst + g_off) = v;
-        } else {
+          *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
+        }
+      } else {
+        // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each
+        for (int t = wt; t < 4 * BM; t += NWORK) {
+          const uint32_t l = static_cast<uint32_t>(t & 31);
+          const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
+          const uint32_t qd = l & 3u;
+          const int64_t grow = p0 + r;
+          const int64_t c0 = cbase + 4 * qd;
           uint2 v = make_uint2(0u, 0u);
-          if (row_ok && c0 < lend) {
+          if (grow < p.P && c0 < lend) {
             const uint32_t c = static_cast<uint32_t>(c0);
             const float4 a = DIST == kUniform
                                  ? uniform4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u)
                                  : gaussian4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u);
             v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
           }
-          *reinterpret_cast<uint2*>(sdst + g_off) = v;
+          *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
         }
       }
       // conversion needs this stage's A tile
-      ok = mbar_wait(full_f(sf), (s / NSF) & 1, ab);
+      ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
       if (!__all_sync(0xffffffffu, ok)) break;
-      const float* stg = reinterpret_cast<const float*>(smem + OFF_F + sf * STAGE_F_BYTES);
-      uint8_t* bhi = smem + OFF_BHI + so * OPB_BYTES;
-      uint8_t* blo = smem + OFF_BLO + so * OPB_BYTES;
-      for (int i = wt; i < 2 * nt; i += NWORK) {
-        const int h = i >= nt ? 1 : 0;
-        const int j = i - h * nt;
-        const int box = j / boxn;
-        const float* src = stg + box * boxn * BK + (8 * h) * boxn + (j - box * boxn);
+      const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
+      uint8_t* bhi = smem + C::OFF_BHI + so * C::OPB;
+      uint8_t* blo = smem + C::OFF_BLO + so * C::OPB;
+      for (int i = wt; i < 2 * cols; i += NWORK) {
+        const int hh = i >= cols ? 1 : 0;
+        const int j = i - hh * cols;   // operand row: instruction j / bh, row j % bh
+        const int box = j / bh;
+        const float* src = stg + box * bh * BK + (8 * hh) * bh + (j - box * bh);
         float a[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = src[e * boxn];
+        for (int e = 0; e < 8; ++e) a[e] = src[e * bh];
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -342,14 +403,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
           lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
         }
-        const uint32_t o = kmaj_off(static_cast<uint32_t>(j), static_cast<uint32_t>(h));
+        const uint32_t o = kmaj_off(static_cast<uint32_t>(j), static_cast<uint32_t>(hh));
         *reinterpret_cast<uint4*>(bhi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(blo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      fence_proxy_async_smem();
+      if (PAIR)
+        fence_proxy_async_cluster();  // the even CTA's MMA reads these operands
+      else
+        fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(full_o(so));
+        if (PAIR)
+          mbar_arrive_cluster(lead_full_o + 8u * so);
+        else
+          mbar_arrive(full_o(so));
         mbar_arrive(empty_f(sf));
       }
     }
@@ -357,11 +424,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // no CTA leaves while its peer may still address it
   if (warp == WARP_MMA) {
     tc_fence_after();
-    drain_wait(drain_bar, 0, 200000000ull);  // every MMA finished before TMEM is freed
     __syncwarp();
-    tmem_dealloc(tmem, static_cast<uint32_t>(p.tmem_cols));
+    if (PAIR)
+      tmem_dealloc_pair(tmem, static_cast<uint32_t>(p.tmem_cols));
+    else
+      tmem_dealloc(tmem, static_cast<uint32_t>(p.tmem_cols));
   }
 }
 
@@ -379,49 +449,100 @@ int num_sms_tc() {
   return sms;
 }
 
+template <bool PAIR>
+cudaError_t set_smem_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kGaussian, PAIR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kRademacher, PAIR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kUniform, PAIR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <bool PAIR>
+void fill_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, dim3 grid, cudaStream_t st) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = grid;
+  cfg->blockDim = dim3(NTHREADS, 1, 1);
+  cfg->dynamicSmemBytes = Cfg<PAIR>::SMEM;
+  cfg->stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PAIR ? 2 : 1;  // a CTA pair must be adjacent in x
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+}
+
+// SMs that can hold CTA pairs of this kernel at once (a pair must fit in one
+// GPC), or -1.
+int64_t pair_slots() {
+  static int64_t cache = 0;
+  if (cache != 0) return cache;
+  if (set_smem_attr<true>() != cudaSuccess) return cache = -1;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config<true>(&cfg, attr, dim3(2, 1, 1), nullptr);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_left<kGaussian, true>, &cfg) !=
+          cudaSuccess ||
+      clusters <= 0) {
+    cudaGetLastError();
+    return cache = -1;
+  }
+  return cache = static_cast<int64_t>(clusters) * 2;
+}
+
 struct Plan {
-  int nt, boxn, nbox, tmem_cols;
-  int64_t tiles_q, tiles_p;
+  bool pair;
+  int nt, tmem_cols, boxw;
+  int64_t tiles_q, tiles_p;  // tiles_p is even for pairs
   int splits;
   int64_t chunk;
 };
 
-// Tile width, TMA boxes and the split-K count: whole waves of one CTA per SM,
-// and no split longer than 2^16 rows of m (4096 MMA K-steps) so that FP32
-// accumulation chains stay short.
+// Tile width, pairing and split-K count: whole waves of one CTA per SM.
 Plan plan_left(const GemmShape& s) {
   Plan pl;
-  if (s.Q > 256) {
-    pl.nt = 512;
-    pl.boxn = 256;
-    pl.nbox = 2;
-  } else {
-    pl.nt = static_cast<int>((s.Q + 15) / 16 * 16);
-    pl.boxn = pl.nt;
-    pl.nbox = 1;
-  }
+  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + 15) / 16 * 16);
   pl.tmem_cols = 32;
   while (pl.tmem_cols < pl.nt) pl.tmem_cols *= 2;
   pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
-  pl.tiles_p = (s.P + BM - 1) / BM;
+  const int64_t tp = (s.P + BM - 1) / BM;
+  int64_t slots = num_sms_tc();
+  pl.pair = false;
+  if (tp >= 2) {
+    const int64_t ps = pair_slots();
+    if (ps > 0) {
+      pl.pair = true;
+      slots = ps;
+    }
+  }
+  const int nh = pl.nt > 256 ? 256 : pl.nt;
+  pl.boxw = pl.pair ? nh / 2 : nh;
+  pl.tiles_p = pl.pair ? (tp + 1) / 2 * 2 : tp;
   const int64_t tiles = pl.tiles_q * pl.tiles_p;
-  const int64_t sms = num_sms_tc();
   const int64_t steps_total = (s.L + BK - 1) / BK;
-  const int64_t smin = 1;
   int64_t smax = steps_total / 8;  // at least 8 stages per split
   if (smax > 128) smax = 128;
-  if (smax < smin) smax = smin;
-  int64_t best = smin;
+  if (smax < 1) smax = 1;
+  int64_t best = 1;
   double best_eff = -1.0;
-  for (int64_t sp = smin; sp <= smax; ++sp) {
+  for (int64_t sp = 1; sp <= smax; ++sp) {
     const int64_t ctas = tiles * sp;
-    const int64_t waves = (ctas + sms - 1) / sms;
-    const double eff = static_cast<double>(ctas) / static_cast<double>(waves * sms);
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = static_cast<double>(ctas) / static_cast<double>(waves * slots);
     if (eff > best_eff + 0.02) {
       best_eff = eff;
       best = sp;
     }
-    if (ctas >= 4 * sms) break;
+    if (ctas >= 4 * slots) break;
   }
   int64_t chunk = (s.L + best - 1) / best;
   chunk = (chunk + BK - 1) / BK * BK;
@@ -443,17 +564,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int DIST>
+template <int DIST, bool PAIR>
 cudaError_t launch_left(const CUtensorMap& map, const TcParams& p, dim3 grid, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_sketch_bf16x2_left<DIST><<<grid, NTHREADS, SMEM_BYTES, st>>>(map, p);
-  return cudaGetLastError();
+  cudaError_t e = set_smem_attr<PAIR>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config<PAIR>(&cfg, attr, grid, st);
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR>, map, p);
+}
+
+template <bool PAIR>
+cudaError_t launch_dist(int dist, const CUtensorMap& map, const TcParams& p, dim3 grid,
+                        cudaStream_t st) {
+  if (dist == kRademacher) return launch_left<kRademacher, PAIR>(map, p, grid, st);
+  if (dist == kUniform) return launch_left<kUniform, PAIR>(map, p, grid, st);
+  return launch_left<kGaussian, PAIR>(map, p, grid, st);
 }
 
 }  // namespace
@@ -483,7 +609,7 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   CUtensorMap map;
   const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(s.Q), static_cast<cuuint64_t>(s.L)};
   const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * sizeof(float)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(pl.boxn), static_cast<cuuint32_t>(BK)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(pl.boxw), static_cast<cuuint32_t>(BK)};
   const cuuint32_t estride[2] = {1, 1};
   CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim,
                     gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -497,8 +623,6 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   p.L = s.L;
   p.chunk = pl.chunk;
   p.nt = pl.nt;
-  p.boxn = pl.boxn;
-  p.nbox = pl.nbox;
   p.tmem_cols = pl.tmem_cols;
   p.key = make_key(h->seed);
   p.status = h->d_status;
@@ -506,16 +630,11 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
   p.part = static_cast<float*>(ws);
-  dim3 grid(static_cast<unsigned>(pl.tiles_q), static_cast<unsigned>(pl.tiles_p),
+  dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
             static_cast<unsigned>(pl.splits));
   prof_mark(h->prof_start, st);
-  cudaError_t e;
-  if (h->dist == kRademacher)
-    e = launch_left<kRademacher>(map, p, grid, st);
-  else if (h->dist == kUniform)
-    e = launch_left<kUniform>(map, p, grid, st);
-  else
-    e = launch_left<kGaussian>(map, p, grid, st);
+  const cudaError_t e = pl.pair ? launch_dist<true>(h->dist, map, p, grid, st)
+                                : launch_dist<false>(h->dist, map, p, grid, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);

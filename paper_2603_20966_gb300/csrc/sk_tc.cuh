@@ -47,15 +47,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // device status word that records why the kernel gave up.
 struct Abort {
   volatile int* flag;  // shared memory
-  int* status;         // global memory (sk_status)
+  int* status;         // global memory: [0] sk_status, [1] site, [2] stage, [3] CTA
   uint64_t limit_ns;
 };
+
+// Site codes recorded in status[1] by the first wait that gives up:
+// role * 16 + barrier, role 1 = TMA producer, 2 = MMA, 3 = epilogue,
+// 4 = worker, 5 = relay; barrier 0 = staging full, 1 = staging empty,
+// 2 = operand full, 3 = operand empty, 4 = accumulator full,
+// 5 = accumulator empty, 6 = MMA stage done.
 
 // Wait until the phase with `parity` of barrier `bar` completed.  Gives up
 // (returns false) when another thread of the CTA raised the abort flag or when
 // `limit_ns` elapsed, in which case it raises the flag and records
 // SK_ETIMEOUT (4) in the status word.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const Abort& ab) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const Abort& ab,
+                                          int site = 0, int stage = 0) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   uint32_t it = 0;
@@ -65,7 +72,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const A
       if (*ab.flag) return false;
       if (globaltimer() - t0 > ab.limit_ns) {
         *ab.flag = 1;
-        atomicExch(ab.status, 4);
+        if (atomicCAS(ab.status, 0, 4) == 0) {  // first give-up of the launch records its site
+          ab.status[1] = site;
+          ab.status[2] = stage;
+          ab.status[3] = static_cast<int>(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y *
+                                                                    blockIdx.z));
+        }
         return false;
       }
     }
@@ -161,6 +173,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- thread-block clusters ----
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// Arrive on an mbarrier given by its shared::cluster address (any CTA of the
+// cluster), with release semantics at cluster scope.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+// All threads of all CTAs of the cluster (warp-aligned).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// ---- CTA pairs (cta_group::2): one MMA spans the tensor cores of two SMs ----
+// The allocation is collective: one warp of each CTA of the pair executes it
+// and both receive the same TMEM address.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// Issued by the even CTA of the pair: A rows 0..M/2-1 and B rows 0..N/2-1 come
+// from its shared memory, the others from the peer's (same offsets); D rows
+// land in the TMEM of the CTA that supplied the A rows.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
 }
 
 // ---- global FP32 accumulation ----
