@@ -171,10 +171,9 @@ sk_status sk_stream_status(sk_handle h, void* stream);
 /* Synchronise `stream` and copy the handle's four device status words
  * without clearing them: [0] the sk_status sk_stream_status would return,
  * [1] where the first bounded wait that gave up was waiting (role * 16 +
- * barrier: roles 1 TMA producer, 2 MMA issuer, 3 epilogue, 4 worker,
- * 5 relay; barriers 0 staging full, 1 staging empty, 2 operand full,
- * 3 operand empty, 4 accumulator full, 5 accumulator empty, 6 MMA stage
- * done), [2] the pipeline stage (or
+ * barrier: roles 1 TMA producer, 2 MMA issuer, 3 epilogue, 4 worker;
+ * barriers 0 staging full, 1 staging empty, 2 operand full, 3 operand empty,
+ * 4 accumulator full, 5 accumulator empty), [2] the pipeline stage (or
  * accumulation chain) it was waiting for, [3] the linear index of its CTA.
  * Words 1-3 are meaningful only when word 0 is SK_ETIMEOUT. */
 sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]);

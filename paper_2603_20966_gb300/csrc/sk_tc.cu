@@ -20,16 +20,16 @@
 //                [16 rows of m] into a staging ring;
 //   warp 1       TMEM allocation (collective over the pair); in the even CTA
 //                the MMA issuer: per stage 2 passes (hi, lo) x NT/256
-//                tcgen05.mma kind::f16 (M=256, K=16) into the FP32 accumulator;
-//   warp 2       relay (even CTA): forwards each stage's and each chain's
-//                completion to the odd CTA;
-//   warps 3-10   epilogue: every CHAIN stages the accumulator is read out of
+//                tcgen05.mma kind::f16 (M=256, K=16) into the FP32
+//                accumulator, completion signalled to both CTAs;
+//   warps 2-9    epilogue: every CHAIN stages the accumulator is read out of
 //                this CTA's TMEM and added into its FP32 partial in global
 //                memory (store for the first chain, red.add after);
-//   warps 11-26  workers: each stage, generate this CTA's BF16 S tile
-//                [128 x 16] (Philox4x32-10 + Box-Muller, or sign bits) and
-//                convert its A columns into hi = bf16(a), lo = bf16(a - hi) in
-//                the K-major no-swizzle operand layout.
+//   warps 10-25  workers, in 4 groups that take turns on successive stages
+//                (so that four stages are in flight): generate this CTA's
+//                BF16 S tile [128 x 16] (Philox4x32-10 + Box-Muller, or sign
+//                bits) and convert its A columns into hi = bf16(a),
+//                lo = bf16(a - hi) in the K-major no-swizzle operand layout.
 // With k <= 128 a single CTA (cta_group::1, M = 128) does the same alone.
 // The tensor core accumulates in FP32 without round-to-nearest on every
 // add, so its error grows with the chain length; restarting the TMEM chain
@@ -58,20 +58,30 @@ constexpr int NT_MAX = 512;   // output columns per tile (TMEM columns)
 constexpr int CHAIN = 128;    // stages per TMEM accumulation chain
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_WORK_WARPS = 16;
+#ifndef SK_TC_GROUPS
+#define SK_TC_GROUPS 4
+#endif
+constexpr int NGROUPS = SK_TC_GROUPS;               // worker groups on alternate stages
+constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
+constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
 constexpr int WARP_TMA = 0;
 constexpr int WARP_MMA = 1;
-constexpr int WARP_RELAY = 2;
-constexpr int WARP_EPI0 = 3;
+constexpr int WARP_EPI0 = 2;
 constexpr int WARP_WORK0 = WARP_EPI0 + NUM_EPI_WARPS;
 constexpr int NWORK = 32 * NUM_WORK_WARPS;
-constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 864
+constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 
 // Per-CTA buffers.  A CTA of a pair holds NT/2 columns of each A tile.
 template <bool PAIR>
 struct Cfg {
   static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // A columns per CTA
-  static constexpr int NSF = PAIR ? 5 : 3;                  // FP32 staging stages
-  static constexpr int NSO = PAIR ? 5 : 3;                  // operand stages
+#ifndef SK_TC_NSF
+  static constexpr int NSF = PAIR ? 6 : 3;                  // FP32 staging stages
+  static constexpr int NSO = PAIR ? 6 : 3;                  // operand stages
+#else
+  static constexpr int NSF = PAIR ? SK_TC_NSF : 3;
+  static constexpr int NSO = PAIR ? SK_TC_NSO : 3;
+#endif
   static constexpr uint32_t STAGE_F = BK * COLS * 4;        // FP32 staging
   static constexpr uint32_t OPB = COLS * BK * 2;            // hi or lo operand
   static constexpr uint32_t OPS = BM * BK * 2;              // S tile
@@ -80,7 +90,7 @@ struct Cfg {
   static constexpr uint32_t OFF_BLO = OFF_BHI + NSO * OPB;
   static constexpr uint32_t OFF_S = OFF_BLO + NSO * OPB;
   static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
-  static constexpr uint32_t NUM_BARS = 2 * NSF + 3 * NSO + 3;
+  static constexpr uint32_t NUM_BARS = 2 * NSF + 2 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
@@ -132,8 +142,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
   auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
   auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
-  auto mma_done = [&](int i) { return bar0 + 8u * (2 * C::NSF + 2 * C::NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 3 * C::NSO);
+  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 2 * C::NSO);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
@@ -159,12 +168,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NSF; ++i) {
       mbar_init(full_f(i), 1);
-      mbar_init(empty_f(i), NUM_WORK_WARPS);
+      mbar_init(empty_f(i), GROUP_WARPS);
     }
     for (int i = 0; i < C::NSO; ++i) {
-      mbar_init(full_o(i), NUM_WORK_WARPS * (PAIR ? 2 : 1));  // workers of both CTAs
+      mbar_init(full_o(i), GROUP_WARPS * (PAIR ? 2 : 1));  // one worker group of each CTA
       mbar_init(empty_o(i), 1);
-      mbar_init(mma_done(i), 1);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_EPI_WARPS * (PAIR ? 2 : 1));  // epilogues of both CTAs
@@ -201,9 +209,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (s >= C::NSF && !mbar_wait(empty_f(sf), ((s / C::NSF) & 1) ^ 1, ab, 0x11, s)) break;
         mbar_arrive_expect_tx(full_f(sf), tx);
         const int32_t y = static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK);
-        for (int h = 0; h < nmma; ++h)
-          tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(h * bh * BK * 4),
-                      &tmapA, static_cast<int32_t>(q0 + h * 256 + static_cast<int>(rank) * bh), y,
+        for (int b = 0; b * 256 < cols; ++b)
+          tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(b * 256 * BK * 4),
+                      &tmapA, static_cast<int32_t>(q0 + static_cast<int>(rank) * cols + b * 256), y,
                       full_f(sf));
         issued = s + 1;
       }
@@ -240,9 +248,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         const bool chain_end = in_chain == CHAIN - 1 || s == nsteps - 1;
-        if (PAIR) {
-          mma_commit_pair(mma_done(so));  // the relay frees the operands of both CTAs
-          if (chain_end) mma_commit_pair(acc_full);
+        if (PAIR) {  // operands and accumulator are both CTAs'
+          mma_commit_pair_both(empty_o(so));
+          if (chain_end) mma_commit_pair_both(acc_full);
         } else {
           mma_commit(empty_o(so));
           if (chain_end) mma_commit(acc_full);
@@ -255,21 +263,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // every MMA has finished before this CTA reaches the closing barrier
       drain_wait(drain_bar, 0, 200000000ull);
     }
-  } else if (warp == WARP_RELAY) {
-    if (PAIR && leader && lane == 0) {
-      const uint32_t peer_empty = mapa_shared(empty_o(0), 1u);
-      const uint32_t peer_acc = mapa_shared(acc_full, 1u);
-      for (int s = 0; s < nsteps; ++s) {
-        const int so = s % C::NSO;
-        if (!mbar_wait(mma_done(so), (s / C::NSO) & 1, ab, 0x56, s)) break;
-        mbar_arrive(empty_o(so));
-        mbar_arrive_cluster(peer_empty + 8u * so);
-        if (s % CHAIN == CHAIN - 1 || s == nsteps - 1) {
-          if (!mbar_wait(acc_full, (s / CHAIN) & 1, ab, 0x54, s)) break;
-          mbar_arrive_cluster(peer_acc);
-        }
-      }
-    }
   } else if (warp < WARP_WORK0) {
     // ---- epilogue: add each finished chain into this CTA's FP32 partial ----
     const int quarter = warp & 3;
@@ -278,36 +271,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t gp = p0 + row;
     float* dst_row = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gp) * p.Q + q0;
     const bool vec_ok = (p.Q % 4) == 0;
-    for (int c = 0; c < nchains; ++c) {
-      const bool ok = mbar_wait(acc_full, c & 1, ab, 0x34, c);
+    for (int c0 = 0; c0 < nchains; ++c0) {
+      const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
       if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld below is warp-collective
       tc_fence_after();
-      for (int ci = colset; ci * 32 < nt; ci += 2) {
+      // TMEM column h*256 + c holds B row c of instruction h: with a pair,
+      // rows c < bh are the even CTA's columns h*bh + c of the tile and rows
+      // c >= bh the odd CTA's columns cols + h*bh + (c - bh)
+      for (int ci = colset; ci * 32 < nmma * 256 && ci * 32 < (nmma - 1) * 256 + nh; ci += 2) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                       static_cast<uint32_t>(ci * 32),
                   v);
         tmem_ld_wait();
         if (gp < p.P) {
-          const int64_t col = q0 + ci * 32;
-          float* d = dst_row + ci * 32;
-          if (vec_ok && col + 32 <= p.Q) {
 #pragma unroll
-            for (int e = 0; e < 32; e += 4) {
-              const float a = __uint_as_float(v[e]), b = __uint_as_float(v[e + 1]);
-              const float x = __uint_as_float(v[e + 2]), y = __uint_as_float(v[e + 3]);
-              if (c == 0)
-                *reinterpret_cast<float4*>(d + e) = make_float4(a, b, x, y);
+          for (int e = 0; e < 32; e += 4) {  // bh is a multiple of 8: groups never straddle
+            const int tcol = ci * 32 + e;
+            const int h = tcol >> 8;
+            const int c = tcol & 255;
+            if (c >= nh) continue;
+            const int tn = PAIR ? (c < bh ? h * bh + c : cols + h * bh + (c - bh)) : tcol;
+            const int64_t col = q0 + tn;
+            float* d = dst_row + tn;
+            const float a0 = __uint_as_float(v[e]), a1 = __uint_as_float(v[e + 1]);
+            const float a2 = __uint_as_float(v[e + 2]), a3 = __uint_as_float(v[e + 3]);
+            if (vec_ok && col + 4 <= p.Q) {
+              if (c0 == 0)
+                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
               else
-                red_add_v4(d + e, a, b, x, y);
-            }
-          } else {
-            for (int e = 0; e < 32; ++e) {
-              if (col + e < p.Q) {
-                if (c == 0)
-                  d[e] = __uint_as_float(v[e]);
-                else
-                  red_add(d + e, __uint_as_float(v[e]));
+                red_add_v4(d, a0, a1, a2, a3);
+            } else {
+              const float vv[4] = {a0, a1, a2, a3};
+              for (int u = 0; u < 4; ++u) {
+                if (col + u < p.Q) {
+                  if (c0 == 0)
+                    d[u] = vv[u];
+                  else
+                    red_add(d + u, vv[u]);
+                }
               }
             }
           }
@@ -324,10 +326,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ---- workers: generate this CTA's S tile and convert its A columns ----
-    const int wt = threadIdx.x - 32 * WARP_WORK0;
+    // group g handles the stages s = g (mod NGROUPS)
+    const int grp = (warp - WARP_WORK0) / GROUP_WARPS;
+    const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * GROUP_THREADS;
     uint32_t cached_blk = 0xffffffffu;
     uint4 words = make_uint4(0u, 0u, 0u, 0u);
-    for (int s = 0; s < nsteps; ++s) {
+    for (int s = grp; s < nsteps; s += NGROUPS) {
       const int sf = s % C::NSF;
       const int so = s % C::NSO;
       // the MMAs that read operand buffer `so` last time have completed
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
       if (DIST == kRademacher) {
         // 128 rows x 2 k-halves, 8 entries each, one Philox call per 128 columns
-        for (int t = wt; t < 2 * BM; t += NWORK) {
+        for (int t = wt; t < 2 * BM; t += GROUP_THREADS) {
           const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
           const uint32_t hh = static_cast<uint32_t>(t >> 7);
           const int64_t grow = p0 + r;
@@ -363,8 +367,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
         }
       } else {
-        // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each
-        for (int t = wt; t < 4 * BM; t += NWORK) {
+        // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each; a
+        // fixed, unrolled count per thread lets independent chains interleave
+        constexpr int GEN_IT = (4 * BM + GROUP_THREADS - 1) / GROUP_THREADS;
+#pragma unroll
+        for (int it = 0; it < GEN_IT; ++it) {
+          const int t = wt + it * GROUP_THREADS;
+          if (t >= 4 * BM) break;
           const uint32_t l = static_cast<uint32_t>(t & 31);
           const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
           const uint32_t qd = l & 3u;
@@ -387,14 +396,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
       uint8_t* bhi = smem + C::OFF_BHI + so * C::OPB;
       uint8_t* blo = smem + C::OFF_BLO + so * C::OPB;
-      for (int i = wt; i < 2 * cols; i += NWORK) {
+      constexpr int CONV_IT = (2 * C::COLS + GROUP_THREADS - 1) / GROUP_THREADS;
+#pragma unroll
+      for (int it = 0; it < CONV_IT; ++it) {
+        const int i = wt + it * GROUP_THREADS;
+        if (i >= 2 * cols) break;
         const int hh = i >= cols ? 1 : 0;
-        const int j = i - hh * cols;   // operand row: instruction j / bh, row j % bh
-        const int box = j / bh;
-        const float* src = stg + box * bh * BK + (8 * hh) * bh + (j - box * bh);
+        const int j = i - hh * cols;   // column j of this CTA's slice = operand row j
+        const int box = j >> 8;        // staging boxes are 256 columns wide
+        const int bw = min(cols - box * 256, 256);
+        const float* src = stg + box * 256 * BK + (8 * hh) * bw + (j - box * 256);
         float a[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = src[e * bh];
+        for (int e = 0; e < 8; ++e) a[e] = src[e * bw];
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -524,8 +538,10 @@ Plan plan_left(const GemmShape& s) {
       slots = ps;
     }
   }
-  const int nh = pl.nt > 256 ? 256 : pl.nt;
-  pl.boxw = pl.pair ? nh / 2 : nh;
+  // each CTA loads one contiguous slice of the tile's columns (half of them
+  // in a pair) as boxes of at most 256 columns
+  const int cta_cols = pl.pair ? pl.nt / 2 : pl.nt;
+  pl.boxw = cta_cols > 256 ? 256 : cta_cols;
   pl.tiles_p = pl.pair ? (tp + 1) / 2 * 2 : tp;
   const int64_t tiles = pl.tiles_q * pl.tiles_p;
   const int64_t steps_total = (s.L + BK - 1) / BK;

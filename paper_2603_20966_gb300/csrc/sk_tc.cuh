@@ -53,9 +53,8 @@ struct Abort {
 
 // Site codes recorded in status[1] by the first wait that gives up:
 // role * 16 + barrier, role 1 = TMA producer, 2 = MMA, 3 = epilogue,
-// 4 = worker, 5 = relay; barrier 0 = staging full, 1 = staging empty,
-// 2 = operand full, 3 = operand empty, 4 = accumulator full,
-// 5 = accumulator empty, 6 = MMA stage done.
+// 4 = worker; barrier 0 = staging full, 1 = staging empty, 2 = operand full,
+// 3 = operand empty, 4 = accumulator full, 5 = accumulator empty.
 
 // Wait until the phase with `parity` of barrier `bar` completed.  Gives up
 // (returns false) when another thread of the CTA raised the abort flag or when
@@ -225,6 +224,14 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, u
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` in both CTAs of the pair once the pair's MMAs completed.
+__device__ __forceinline__ void mma_commit_pair_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(static_cast<uint16_t>(3))
       : "memory");
 }
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
