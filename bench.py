@@ -68,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -106,6 +106,27 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_traffic():
+    """DRAM bytes per benchmarked launch of the fused kernel from the committed
+    ncu summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_sketch_bf16x2_left_pair_m2e18.md")
+    src = os.path.join(ROOT, "paper_2603_20966_gb300", "csrc", "sk_tc.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    rec = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and
+               line.split(": ", 1)[0] in ("kernel_source_sha256_16", "traffic_bytes_per_full_launch"))
+    if rec.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(rec["traffic_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def dist_env():
@@ -259,7 +280,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "peak_kind": f"{pk_kind} bf16 burst",
                 "note": "achieved counts both split-A MMA passes (4 k m n flop per sketch)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic() if (form != P.SK_FP32 and args.workload == "C2") else None
     roof["kernel_ms_by_dist"] = {DIST_NAME[d]: statistics.mean(kernel_ms[j::len(dists)])
                                  for j, d in enumerate(dists)}
 
@@ -328,7 +349,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16x2", choices=["fp32", "bf16x2"])

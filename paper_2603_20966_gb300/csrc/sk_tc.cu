@@ -58,12 +58,7 @@ constexpr int NT_MAX = 512;   // output columns per tile (TMEM columns)
 constexpr int CHAIN = 128;    // stages per TMEM accumulation chain
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_WORK_WARPS = 16;
-#ifndef SK_TC_GROUPS
-#define SK_TC_GROUPS 4
-#endif
-constexpr int NGROUPS = SK_TC_GROUPS;               // worker groups on alternate stages
-constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
-constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
+
 constexpr int WARP_TMA = 0;
 constexpr int WARP_MMA = 1;
 constexpr int WARP_EPI0 = 2;
@@ -75,6 +70,13 @@ constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 template <bool PAIR>
 struct Cfg {
   static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // A columns per CTA
+  // Worker groups take turns on successive stages.  A group that starts
+  // stage s has finished stage s - NGROUPS, so waits never run more than one
+  // barrier phase ahead (the parity test would alias) as long as
+  // NGROUPS <= NSF and NGROUPS <= NSO.
+  static constexpr int NGROUPS = PAIR ? 4 : 2;
+  static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
+  static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
 #ifndef SK_TC_NSF
   static constexpr int NSF = PAIR ? 6 : 3;                  // FP32 staging stages
   static constexpr int NSO = PAIR ? 6 : 3;                  // operand stages
@@ -94,6 +96,7 @@ struct Cfg {
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(NGROUPS <= NSF && NGROUPS <= NSO, "worker groups vs ring depth");
 };
 
 // K-major no-swizzle operand layout (16-element K slab): core matrix
@@ -168,10 +171,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NSF; ++i) {
       mbar_init(full_f(i), 1);
-      mbar_init(empty_f(i), GROUP_WARPS);
+      mbar_init(empty_f(i), C::GROUP_WARPS);
     }
     for (int i = 0; i < C::NSO; ++i) {
-      mbar_init(full_o(i), GROUP_WARPS * (PAIR ? 2 : 1));  // one worker group of each CTA
+      mbar_init(full_o(i), C::GROUP_WARPS * (PAIR ? 2 : 1));  // one worker group of each CTA
       mbar_init(empty_o(i), 1);
     }
     mbar_init(acc_full, 1);
@@ -326,12 +329,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ---- workers: generate this CTA's S tile and convert its A columns ----
-    // group g handles the stages s = g (mod NGROUPS)
-    const int grp = (warp - WARP_WORK0) / GROUP_WARPS;
-    const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * GROUP_THREADS;
-    uint32_t cached_blk = 0xffffffffu;
-    uint4 words = make_uint4(0u, 0u, 0u, 0u);
-    for (int s = grp; s < nsteps; s += NGROUPS) {
+    // group g handles the stages s = g (mod C::NGROUPS)
+    const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
+    const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
+    // Rademacher: each thread keeps the same (row, half) tasks on every stage
+    // and caches their Philox words across the 8 stages a call covers
+    constexpr int RAD_IT = (2 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    uint32_t cached_blk[RAD_IT];
+    uint4 words[RAD_IT];
+#pragma unroll
+    for (int it = 0; it < RAD_IT; ++it) {
+      cached_blk[it] = 0xffffffffu;
+      words[it] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int s = grp; s < nsteps; s += C::NGROUPS) {
       const int sf = s % C::NSF;
       const int so = s % C::NSO;
       // the MMAs that read operand buffer `so` last time have completed
@@ -341,7 +352,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
       if (DIST == kRademacher) {
         // 128 rows x 2 k-halves, 8 entries each, one Philox call per 128 columns
-        for (int t = wt; t < 2 * BM; t += GROUP_THREADS) {
+#pragma unroll
+        for (int it = 0; it < RAD_IT; ++it) {
+          const int t = wt + it * C::GROUP_THREADS;
+          if (t >= 2 * BM) break;
           const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
           const uint32_t hh = static_cast<uint32_t>(t >> 7);
           const int64_t grow = p0 + r;
@@ -350,13 +364,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (grow < p.P && c0 < lend) {
             const uint32_t c = static_cast<uint32_t>(c0);
             const uint32_t blk = c >> 7;
-            if (blk != cached_blk) {  // the same thread keeps the same (row, half)
-              words = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
-              cached_blk = blk;
+            if (blk != cached_blk[it]) {
+              words[it] = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
+              cached_blk[it] = blk;
             }
             const uint32_t wsel = (c >> 5) & 3u;
-            const uint32_t w = wsel == 0 ? words.x : wsel == 1 ? words.y
-                             : wsel == 2 ? words.z : words.w;
+            const uint4 wv = words[it];
+            const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
             const uint32_t bits = w >> (c & 31u);
             // +1.0 = 0x3F80, -1.0 = 0xBF80: the sign bit carries the random bit
             v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
@@ -369,10 +383,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       } else {
         // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each; a
         // fixed, unrolled count per thread lets independent chains interleave
-        constexpr int GEN_IT = (4 * BM + GROUP_THREADS - 1) / GROUP_THREADS;
+        constexpr int GEN_IT = (4 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
         for (int it = 0; it < GEN_IT; ++it) {
-          const int t = wt + it * GROUP_THREADS;
+          const int t = wt + it * C::GROUP_THREADS;
           if (t >= 4 * BM) break;
           const uint32_t l = static_cast<uint32_t>(t & 31);
           const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
@@ -396,10 +410,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
       uint8_t* bhi = smem + C::OFF_BHI + so * C::OPB;
       uint8_t* blo = smem + C::OFF_BLO + so * C::OPB;
-      constexpr int CONV_IT = (2 * C::COLS + GROUP_THREADS - 1) / GROUP_THREADS;
+      constexpr int CONV_IT = (2 * C::COLS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
       for (int it = 0; it < CONV_IT; ++it) {
-        const int i = wt + it * GROUP_THREADS;
+        const int i = wt + it * C::GROUP_THREADS;
         if (i >= 2 * cols) break;
         const int hh = i >= cols ? 1 : 0;
         const int j = i - hh * cols;   // column j of this CTA's slice = operand row j
