@@ -464,6 +464,324 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Right sketch Y[m x k] = A[m x n] S^T (S[k x n]) on CTA pairs.
+//
+// The roles of the operands swap: the converted A tile is the MMA's A
+// operand (K-major as stored, no transpose), the generated S tile its B
+// operand.  A pair owns 512 rows of m: each CTA converts 256 of them and holds
+// two TMEM accumulators (m rows 0-127 and 128-255 of its share), so one
+// generated S tile serves 512 rows of A.  Each CTA generates half of the
+// tile's k rows (the pair MMA splits N between the two CTAs).  Warp roles,
+// rings, chains and bounded waits are those of the left kernel.
+// ---------------------------------------------------------------------------
+struct CfgR {
+  static constexpr int ROWS = 256;  // rows of A per CTA (two 128-row accumulators)
+  static constexpr int NGROUPS = 4;
+  static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
+  static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
+  static constexpr int NSF = 6;
+  static constexpr int NSO = 6;
+  static constexpr uint32_t STAGE_F = BK * ROWS * 4;  // FP32 staging [256 rows][16]
+  static constexpr uint32_t OPA = ROWS * BK * 2;      // hi or lo operand, 2 x 4 KB
+  static constexpr uint32_t OPS = 128 * BK * 2;       // this CTA's half of the S tile
+  static constexpr uint32_t OFF_F = 0;
+  static constexpr uint32_t OFF_AHI = OFF_F + NSF * STAGE_F;
+  static constexpr uint32_t OFF_ALO = OFF_AHI + NSO * OPA;
+  static constexpr uint32_t OFF_S = OFF_ALO + NSO * OPA;
+  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
+  static constexpr uint32_t NUM_BARS = 2 * NSF + 2 * NSO + 3;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
+  static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(NGROUPS <= NSF && NGROUPS <= NSO, "worker groups vs ring depth");
+};
+
+struct TcRightParams {
+  float* part;      // partials [splits][P][Q]
+  int64_t P, Q, L;  // P = m, Q = k, L = n
+  int64_t chunk;    // contracted length per split (multiple of BK)
+  int nq;           // N of the MMA: k rows per pair tile (multiple of 16, <= 256)
+  int tmem_cols;    // power of two >= 2 * nq
+  PhiloxKey key;
+  int* status;
+  uint64_t timeout_ns;
+};
+
+template <int DIST>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_sketch_bf16x2_right(const __grid_constant__ CUtensorMap tmapA, const TcRightParams p) {
+  using C = CfgR;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar0 = sbase + C::OFF_BAR;
+  auto full_f = [&](int i) { return bar0 + 8u * i; };
+  auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
+  auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
+  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 2 * C::NSO);
+  const uint32_t acc_empty = acc_full + 8u;
+  const uint32_t drain_bar = acc_full + 16u;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank() & 1u;  // 0 = even CTA (MMA issuer)
+  const bool leader = rank == 0;
+  const int nq = p.nq;
+  const int gh = nq / 2;                                       // S rows this CTA generates
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * C::ROWS;  // this CTA's rows of A
+  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nq;       // the pair's k rows
+  const int64_t g0 = q0 + static_cast<int64_t>(rank) * gh;        // this CTA's S rows
+  const int64_t lbeg = static_cast<int64_t>(blockIdx.z) * p.chunk;
+  const int64_t lend = min(p.L, lbeg + p.chunk);
+  const int nsteps = static_cast<int>((lend - lbeg + BK - 1) / BK);
+  const int nchains = (nsteps + CHAIN - 1) / CHAIN;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NSF; ++i) {
+      mbar_init(full_f(i), 1);
+      mbar_init(empty_f(i), C::GROUP_WARPS);
+    }
+    for (int i = 0; i < C::NSO; ++i) {
+      mbar_init(full_o(i), C::GROUP_WARPS * 2);
+      mbar_init(empty_o(i), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NUM_EPI_WARPS * 2);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == WARP_MMA) {
+    tmem_alloc_pair(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+    tmem_relinquish_pair();
+  }
+  if (warp == WARP_TMA && lane == 0) tma_prefetch_desc(&tmapA);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const Abort ab{abort_flag, p.status, p.timeout_ns};
+  const uint32_t lead_full_o = mapa_shared(full_o(0), 0u);
+  const uint32_t lead_acc_empty = mapa_shared(acc_empty, 0u);
+
+  if (warp == WARP_TMA) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nsteps; ++s) {
+        const int sf = s % C::NSF;
+        if (s >= C::NSF && !mbar_wait(empty_f(sf), ((s / C::NSF) & 1) ^ 1, ab, 0x11, s)) break;
+        mbar_arrive_expect_tx(full_f(sf), C::STAGE_F);
+        tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F, &tmapA,
+                    static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK),
+                    static_cast<int32_t>(m0), full_f(sf));
+        issued = s + 1;
+      }
+      if (*abort_flag) {
+        for (int s = max(0, issued - C::NSF); s < issued; ++s)
+          drain_wait(full_f(s % C::NSF), (s / C::NSF) & 1, 100000000ull);
+      }
+    }
+  } else if (warp == WARP_MMA) {
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_bf16_f32(256u, static_cast<uint32_t>(nq));
+      for (int s = 0; s < nsteps; ++s) {
+        const int so = s % C::NSO;
+        const int in_chain = s % CHAIN;
+        if (s > 0 && in_chain == 0 &&
+            !mbar_wait(acc_empty, ((s / CHAIN) - 1) & 1, ab, 0x25, s))
+          break;
+        if (!mbar_wait(full_o(so), (s / C::NSO) & 1, ab, 0x22, s)) break;
+        tc_fence_after();
+        const uint64_t bdesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const uint32_t ab_ = sbase + (pass ? C::OFF_ALO : C::OFF_AHI) + so * C::OPA;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint64_t adesc = smem_desc(ab_ + static_cast<uint32_t>(j) * (C::OPA / 2), LBO, SBO);
+            mma_bf16_pair(tmem + static_cast<uint32_t>(j * nq), adesc, bdesc, idesc,
+                          (in_chain > 0 || pass > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit_pair_both(empty_o(so));
+        if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit_pair_both(acc_full);
+      }
+      mma_commit_pair(drain_bar);
+      drain_wait(drain_bar, 0, 200000000ull);
+    }
+  } else if (warp < WARP_WORK0) {
+    // ---- epilogue: accumulator j holds rows m0 + 128 j + lane, columns q0 + c ----
+    const int quarter = warp & 3;
+    const int colset = (warp - WARP_EPI0) >> 2;
+    const bool vec_ok = (p.Q % 4) == 0;
+    const int nchunk = (nq + 31) / 32;
+    for (int c0 = 0; c0 < nchains; ++c0) {
+      const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      for (int t = colset; t < 2 * nchunk; t += 2) {
+        const int j = t / nchunk;
+        const int ci = t - j * nchunk;
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                      static_cast<uint32_t>(j * nq + ci * 32),
+                  v);
+        tmem_ld_wait();
+        const int64_t gm = m0 + j * 128 + quarter * 32 + lane;
+        if (gm < p.P) {
+          float* drow = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + q0;
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const int c = ci * 32 + e;
+            if (c >= nq) continue;
+            const int64_t col = q0 + c;
+            const float a0 = __uint_as_float(v[e]), a1 = __uint_as_float(v[e + 1]);
+            const float a2 = __uint_as_float(v[e + 2]), a3 = __uint_as_float(v[e + 3]);
+            float* d = drow + c;
+            if (vec_ok && col + 4 <= p.Q) {
+              if (c0 == 0)
+                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+              else
+                red_add_v4(d, a0, a1, a2, a3);
+            } else {
+              const float vv[4] = {a0, a1, a2, a3};
+              for (int u = 0; u < 4; ++u) {
+                if (col + u < p.Q) {
+                  if (c0 == 0)
+                    d[u] = vv[u];
+                  else
+                    red_add(d + u, vv[u]);
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
+    }
+  } else {
+    // ---- workers: this CTA's half of the S tile, and its 256 rows of A ----
+    const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
+    const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
+    constexpr int RAD_IT = (2 * 128 + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    uint32_t cached_blk[RAD_IT];
+    uint4 words[RAD_IT];
+#pragma unroll
+    for (int it = 0; it < RAD_IT; ++it) {
+      cached_blk[it] = 0xffffffffu;
+      words[it] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int s = grp; s < nsteps; s += C::NGROUPS) {
+      const int sf = s % C::NSF;
+      const int so = s % C::NSO;
+      bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
+      const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
+      if (DIST == kRademacher) {
+#pragma unroll
+        for (int it = 0; it < RAD_IT; ++it) {
+          const int t = wt + it * C::GROUP_THREADS;
+          if (t >= 2 * gh) break;
+          const uint32_t r = static_cast<uint32_t>(t % gh);
+          const uint32_t hh = static_cast<uint32_t>(t / gh);
+          const int64_t grow = g0 + r;
+          const int64_t c0 = cbase + 8 * hh;
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (grow < p.Q && c0 < lend) {
+            const uint32_t c = static_cast<uint32_t>(c0);
+            const uint32_t blk = c >> 7;
+            if (blk != cached_blk[it]) {
+              words[it] = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
+              cached_blk[it] = blk;
+            }
+            const uint32_t wsel = (c >> 5) & 3u;
+            const uint4 wv = words[it];
+            const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
+            const uint32_t bits = w >> (c & 31u);
+            v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
+            v.y = 0x3F803F80u | ((bits & 4u) << 13) | ((bits & 8u) << 28);
+            v.z = 0x3F803F80u | ((bits & 16u) << 11) | ((bits & 32u) << 26);
+            v.w = 0x3F803F80u | ((bits & 64u) << 9) | ((bits & 128u) << 24);
+          }
+          *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
+        }
+      } else {
+        constexpr int GEN_IT = (4 * 128 + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+#pragma unroll
+        for (int it = 0; it < GEN_IT; ++it) {
+          const int t = wt + it * C::GROUP_THREADS;
+          if (t >= 4 * gh) break;
+          const uint32_t l = static_cast<uint32_t>(t & 31);
+          const uint32_t qd = l & 3u;
+          const uint32_t r = static_cast<uint32_t>(t >> 2);  // row, 4 quads per row
+          const int64_t grow = g0 + r;
+          const int64_t c0 = cbase + 4 * qd;
+          uint2 v = make_uint2(0u, 0u);
+          if (grow < p.Q && c0 < lend) {
+            const uint32_t c = static_cast<uint32_t>(c0);
+            const float4 a = DIST == kUniform
+                                 ? uniform4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u)
+                                 : gaussian4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u);
+            v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
+          }
+          *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
+        }
+      }
+      ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
+      uint8_t* ahi = smem + C::OFF_AHI + so * C::OPA;
+      uint8_t* alo = smem + C::OFF_ALO + so * C::OPA;
+      constexpr int CONV_IT = (2 * C::ROWS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+#pragma unroll
+      for (int it = 0; it < CONV_IT; ++it) {
+        const int i = wt + it * C::GROUP_THREADS;
+        const int row = i >> 1;   // 0..255: accumulator row / 128, lane row % 128
+        const int hh = i & 1;
+        const float4 x0 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh);
+        const float4 x1 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh + 4);
+        const float a[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
+          const float h0 = __uint_as_float(hw[e] << 16);
+          const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
+          lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
+        }
+        const uint32_t o = static_cast<uint32_t>(row >> 7) * (C::OPA / 2) +
+                           kmaj_off(static_cast<uint32_t>(row & 127), static_cast<uint32_t>(hh));
+        *reinterpret_cast<uint4*>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_proxy_async_cluster();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_cluster(lead_full_o + 8u * so);
+        mbar_arrive(empty_f(sf));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == WARP_MMA) {
+    tc_fence_after();
+    __syncwarp();
+    tmem_dealloc_pair(tmem, static_cast<uint32_t>(p.tmem_cols));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int num_sms_tc() {
@@ -612,17 +930,81 @@ cudaError_t launch_dist(int dist, const CUtensorMap& map, const TcParams& p, dim
   return launch_left<kGaussian, PAIR>(map, p, grid, st);
 }
 
+cudaError_t set_smem_attr_right() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_right<kGaussian>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, CfgR::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_bf16x2_right<kRademacher>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CfgR::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_bf16x2_right<kUniform>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CfgR::SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// Right sketch: pairs of CTAs own 512 rows of m and nq <= 256 rows of k; the
+// split count keeps the partials (splits x m x k floats) to a few hundred MB.
+Plan plan_right(const GemmShape& s) {
+  Plan pl;
+  pl.pair = true;
+  pl.nt = s.Q > 256 ? 256 : static_cast<int>((s.Q + 15) / 16 * 16);
+  pl.tmem_cols = 32;
+  while (pl.tmem_cols < 2 * pl.nt) pl.tmem_cols *= 2;
+  pl.boxw = BK;
+  pl.tiles_p = (s.P + 2 * CfgR::ROWS - 1) / (2 * CfgR::ROWS) * 2;  // CTAs along m
+  pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
+  int64_t slots = pair_slots();
+  if (slots <= 0) slots = num_sms_tc();
+  const int64_t tiles = pl.tiles_p * pl.tiles_q;
+  const int64_t steps_total = (s.L + BK - 1) / BK;
+  int64_t smax = steps_total / 8;
+  const int64_t part_bytes = s.P * s.Q * 4;
+  const int64_t cap = part_bytes > 0 ? (int64_t(1) << 29) / part_bytes : 128;
+  if (smax > cap) smax = cap;
+  if (smax > 128) smax = 128;
+  if (smax < 1) smax = 1;
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int64_t sp = 1; sp <= smax; ++sp) {
+    const int64_t ctas = tiles * sp;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = static_cast<double>(ctas) / static_cast<double>(waves * slots);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+  }
+  int64_t chunk = (s.L + best - 1) / best;
+  chunk = (chunk + BK - 1) / BK * BK;
+  pl.chunk = chunk;
+  pl.splits = static_cast<int>((s.L + chunk - 1) / chunk);
+  return pl;
+}
+
+template <int DIST>
+cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 grid,
+                         cudaStream_t st) {
+  cudaError_t e = set_smem_attr_right();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config<true>(&cfg, attr, grid, st);
+  cfg.dynamicSmemBytes = CfgR::SMEM;
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_right<DIST>, map, p);
+}
+
 }  // namespace
 
 size_t tc_workspace_bytes(const GemmShape& s) {
-  if (!s.left) return 0;
-  const Plan pl = plan_left(s);
+  const Plan pl = s.left ? plan_left(s) : plan_right(s);
   return static_cast<size_t>(pl.splits) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
          sizeof(float);
 }
 
 sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float* Y, int64_t ldy) {
-  if (!s.left) return SK_EUNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(Y) & 15u))
     return SK_EINVAL;
   if (lda % 4 != 0 || ldy % 4 != 0) return SK_EINVAL;
@@ -630,9 +1012,54 @@ sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float*
   return SK_OK;
 }
 
+cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                            float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const Plan pl = plan_right(s);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  CUtensorMap map;
+  // A[m x n]: n innermost; one box = 16 columns of n x 256 rows of m
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(s.L), static_cast<cuuint64_t>(s.P)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * sizeof(float)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(CfgR::ROWS)};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim,
+                    gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  TcRightParams p;
+  p.P = s.P;
+  p.Q = s.Q;
+  p.L = s.L;
+  p.chunk = pl.chunk;
+  p.nq = pl.nt;
+  p.tmem_cols = pl.tmem_cols;
+  p.key = make_key(h->seed);
+  p.status = h->d_status;
+  p.timeout_ns = 2000000000ull;
+  const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
+  if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
+  p.part = static_cast<float*>(ws);
+  dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
+            static_cast<unsigned>(pl.splits));
+  prof_mark(h->prof_start, st);
+  cudaError_t e;
+  if (h->dist == kRademacher)
+    e = launch_right<kRademacher>(map, p, grid, st);
+  else if (h->dist == kUniform)
+    e = launch_right<kUniform>(map, p, grid, st);
+  else
+    e = launch_right<kGaussian>(map, p, grid, st);
+  prof_mark(h->prof_stop, st);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  return splitk_reduce(static_cast<float*>(ws), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+}
+
 cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                       float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (!s.left) return cudaErrorNotSupported;
+  if (!s.left) return tc_sketch_right(h, s, A, lda, Y, ldy, ws, ws_bytes, st);
   const Plan pl = plan_left(s);
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (enc == nullptr) return cudaErrorNotSupported;

@@ -128,3 +128,64 @@ def test_full_size_tall_skinny_sampled(P, orc, dist):
     err = rel_frob(got, ref)
     assert err <= TOL, err
     assert torch.isfinite(Y).all()
+
+
+def run_right(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
+    m, n = A.shape
+    lda = lda or (n + 3) // 4 * 4
+    ldy = ldy or (k + 3) // 4 * 4
+    Ad = torch.zeros((m, lda), dtype=torch.float32, device="cuda")
+    Ad[:, :n] = A.cuda()
+    Y = torch.full((m, ldy), float("nan"), dtype=torch.float32, device="cuda")
+    h = P.sk_create(seed, dist, k)
+    try:
+        P.sk_set_precision(h, prec)
+        P.sk_apply_right(h, Ad, m, n, lda, Y, ldy)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    return Y[:, :k].cpu().numpy()
+
+
+RIGHT_SHAPES = [(512, 4096, 256), (1000, 3000, 100), (300, 17, 31), (5, 5, 3), (2048, 1000, 512),
+                (700, 70000, 48), (4096, 2048, 256)]
+
+
+@pytest.mark.parametrize("dist", [R, G])
+@pytest.mark.parametrize("m,n,k", RIGHT_SHAPES)
+def test_right_bf16x2_matches_oracle(P, orc, dist, m, n, k):
+    A = _A(m, n, 17 * k + m + n)
+    got = run_right(P, 11, dist, k, A)
+    assert np.all(np.isfinite(got))
+    ref = orc.apply_right(11, dist, BF16, k, A.numpy())
+    err = rel_frob(got, ref)
+    assert err <= TOL, err
+
+
+def test_right_identity_gives_transposed_scaled_matrix(P, orc):
+    n, k = 384, 200
+    got = run_right(P, 5, G, k, torch.eye(n))
+    ref = (orc.generate(5, G, BF16, 0, 0, k, n) * orc.scale(k)).T  # Y = S^T scaled
+    np.testing.assert_array_equal(got, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("dist", [G, R])
+def test_right_full_size_lowrank_sampled(P, orc, dist):
+    # A = U V^T + 1e-3 E, 65536 x 16384, k = 256: the right-sketch workload
+    from paper_2603_20966_gb300.workloads import lowrank_plus_noise
+    m, n, k = 65536, 16384, 256
+    A = lowrank_plus_noise(m, n, device="cuda")
+    Y = torch.empty((m, k), device="cuda")
+    h = P.sk_create(7, dist, k)
+    try:
+        P.sk_set_precision(h, BF16)
+        P.sk_apply_right(h, A, m, n, n, Y, k)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    rows = np.array([0, 1, 511, 512, 30000, 65535])
+    a_rows = A[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ref = orc.apply_right(7, dist, BF16, k, a_rows)
+    got = Y[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert rel_frob(got, ref) <= TOL
+    assert torch.isfinite(Y).all()
