@@ -32,9 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (m, n, k, dists)
-    "C2": (1 << 20, 512, 2048, (1, 0)),
-    "C1": (4096, 256, 64, (0,)),
+    # name: (m, n, k, dists, side)
+    "C2": (1 << 20, 512, 2048, (1, 0), "left"),
+    "C1": (4096, 256, 64, (0,), "left"),
+    "C3": (65536, 16384, 256, (0,), "right"),
 }
 DIST_NAME = {0: "gaussian", 1: "rademacher", 2: "uniform"}
 METRIC = "fused gen+sketch TFLOP/s and % roofline vs plain FP32; served p50/p99 latency"
@@ -136,16 +137,23 @@ def dist_env():
     return rank, world, local
 
 
-def oracle_sample(m, n, k, dists, a_cols, seed, rows, nthreads=None):
-    """Time the CPU oracle on `rows` rows x a_cols.shape[1] columns of Y for
-    each distribution.  Returns (seconds, useful flops, threads)."""
+def oracle_sample(m, n, k, dists, a_part, seed, rows, nthreads=None, side="left"):
+    """Time the CPU oracle on a sample of Y for each distribution.  Left:
+    `rows` rows of Y x the a_part.shape[1] columns of A given.  Right: all k
+    columns of Y for the a_part.shape[0] rows of A given.  Returns
+    (seconds, useful flops, threads)."""
     import oracle
     nthreads = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
     for d in dists:
-        oracle.apply_left(seed, d, 0, k, a_cols, nthreads=nthreads, rows=(0, rows))
+        if side == "left":
+            oracle.apply_left(seed, d, 0, k, a_part, nthreads=nthreads, rows=(0, rows))
+        else:
+            oracle.apply_right(seed, d, 0, k, a_part, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return dt, 2.0 * rows * m * a_cols.shape[1] * len(dists), nthreads
+    if side == "left":
+        return dt, 2.0 * rows * m * a_part.shape[1] * len(dists), nthreads
+    return dt, 2.0 * a_part.shape[0] * n * k * len(dists), nthreads
 
 
 def run_reference(args):
@@ -156,14 +164,20 @@ def run_reference(args):
     import torch
 
     from paper_2603_20966_gb300.workloads import gaussian_matrix
-    m, n, k, dists = WORKLOADS[args.workload]
-    ncols, rows = (2, 512) if args.workload == "C2" else (n, k)
-    a_cols = gaussian_matrix(m, ncols, 1, device="cpu").numpy()
+    m, n, k, dists, side = WORKLOADS[args.workload]
+    if side == "left":
+        ncols, rows = (2, 512) if args.workload == "C2" else (n, k)
+        a_part = gaussian_matrix(m, ncols, 1, device="cpu").numpy()
+        what = f"{rows} of {k} rows x {ncols} of {n} columns of Y"
+    else:
+        rows = 16
+        a_part = gaussian_matrix(rows, n, 1, device="cpu").numpy()
+        what = f"{rows} of {m} rows x all {k} columns of Y"
     for _ in range(args.warmup):
-        oracle_sample(m, n, k, dists, a_cols, 7, rows)
+        oracle_sample(m, n, k, dists, a_part, 7, rows, side=side)
     tot, flops, threads = 0.0, 0.0, 1
     for _ in range(args.steps):
-        dt, fl, threads = oracle_sample(m, n, k, dists, a_cols, 7, rows)
+        dt, fl, threads = oracle_sample(m, n, k, dists, a_part, 7, rows, side=side)
         tot += dt
         flops += fl
     value = flops / tot / 1e12
@@ -172,11 +186,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} left sketch A {m}x{n} k={k} "
+        "config": {"workload": f"{args.workload} {side} sketch A {m}x{n} k={k} "
                    f"dists={[DIST_NAME[d] for d in dists]}", "m": m, "n": n, "k": k},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{rows} of {k} rows x {ncols} of {n} columns of Y per "
-                                   f"distribution per step (FP64 accumulation)"},
+                         "sample": f"{what} per distribution per step (FP64 accumulation)"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -197,12 +210,20 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if world > 1:
         tdist.init_process_group("nccl", device_id=dev)
-    m, n, k, dists = WORKLOADS[args.workload]
+    m, n, k, dists, side = WORKLOADS[args.workload]
     form = {"fp32": P.SK_FP32, "bf16x2": P.SK_BF16X2}[args.form]
     stream = torch.cuda.current_stream(dev)
+    apply = P.sk_apply_left if side == "left" else P.sk_apply_right
+    apply_host = P.sk_apply_left_host if side == "left" else P.sk_apply_right_host
+    yshape = (k, n) if side == "left" else (m, k)
 
-    A = gaussian_matrix(m, n, 1 + rank, device=dev)
-    Ys = {d: torch.empty((k, n), dtype=torch.float32, device=dev) for d in dists}
+    if args.workload == "C3":
+        from paper_2603_20966_gb300.workloads import lowrank_plus_noise
+        A = lowrank_plus_noise(m, n, device=dev, seeds=(11 + 3 * rank, 12 + 3 * rank,
+                                                        13 + 3 * rank))
+    else:
+        A = gaussian_matrix(m, n, 1 + rank, device=dev)
+    Ys = {d: torch.empty(yshape, dtype=torch.float32, device=dev) for d in dists}
     hs = {}
     for d in dists:
         hs[d] = P.sk_create(7, d, k)
@@ -210,7 +231,7 @@ def run_ours(args):
 
     def step():
         for d in dists:
-            P.sk_apply_left(hs[d], A, m, n, n, Ys[d], n, stream)
+            apply(hs[d], A, m, n, n, Ys[d], yshape[1], stream)
 
     for _ in range(args.warmup):
         step()
@@ -242,7 +263,7 @@ def run_ours(args):
     for _ in range(args.steps):
         for d in dists:
             P.sk_profile_events(hs[d], ev[i][0], ev[i][1])
-            P.sk_apply_left(hs[d], A, m, n, n, Ys[d], n, stream)
+            apply(hs[d], A, m, n, n, Ys[d], yshape[1], stream)
             i += 1
     t_stop.record(stream)
     torch.cuda.synchronize(dev)
@@ -273,6 +294,13 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": flops_per_sketch / avg_kernel_s / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x "
                                                 "max SM clock"}
+    elif side == "right":
+        # HBM-bound: A read once, Y written once
+        algo_bytes = 4.0 * m * n + 4.0 * m * k
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": algo_bytes / avg_kernel_s / 1e9, "peak": peak,
+                "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth",
+                "note": "achieved = (A bytes + Y bytes) / kernel time"}
     else:
         mma = 2 * flops_per_sketch  # split-A: two BF16 MMA passes
         peak = pk["bf16_tflops"]
@@ -289,11 +317,11 @@ def run_ours(args):
     if not args.no_e2e:
         A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         A_host.copy_(A)
-        Y_host = {d: torch.empty((k, n), dtype=torch.float32, pin_memory=True) for d in dists}
+        Y_host = {d: torch.empty(yshape, dtype=torch.float32, pin_memory=True) for d in dists}
 
         def e2e_step():
             for d in dists:
-                P.sk_apply_left_host(hs[d], A_host, m, n, n, Y_host[d], n, stream)
+                apply_host(hs[d], A_host, m, n, n, Y_host[d], yshape[1], stream)
 
         for _ in range(max(1, min(args.warmup, 2))):
             e2e_step()
@@ -310,19 +338,26 @@ def run_ours(args):
             dt = float(t.item())
         e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": len(dists) * m * n * 4,
-               "d2h_bytes_per_step": len(dists) * k * n * 4, "steps": e_steps,
+               "d2h_bytes_per_step": len(dists) * yshape[0] * yshape[1] * 4, "steps": e_steps,
                "ms_per_step": dt / e_steps * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ncols, rows = (16, 2048) if args.workload == "C2" else (n, k)
-        cols = np.linspace(0, n - 1, ncols).astype(np.int64)
-        a_cols = A[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
-        dt, fl, threads = oracle_sample(m, n, k, dists, a_cols, 7, rows)
+        if side == "left":
+            ncols, rows = (16, 2048) if args.workload == "C2" else (n, k)
+            cols = np.linspace(0, n - 1, ncols).astype(np.int64)
+            a_part = A[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
+            what = f"{rows} of {k} rows x {ncols} of {n} columns of Y"
+        else:
+            rows = 256
+            idx = np.linspace(0, m - 1, rows).astype(np.int64)
+            a_part = A[torch.from_numpy(idx).to(dev)].cpu().numpy()
+            what = f"{rows} of {m} rows x all {k} columns of Y"
+        dt, fl, threads = oracle_sample(m, n, k, dists, a_part, 7, rows, side=side)
         cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-               "sample": f"{rows} of {k} rows x {ncols} of {n} columns of Y for each of "
-                         f"{[DIST_NAME[d] for d in dists]} (FP64 accumulation), "
-                         f"{dt:.1f} s; rate extrapolates to the full workload"}
+               "sample": f"{what} for each of {[DIST_NAME[d] for d in dists]} "
+                         f"(FP64 accumulation), {dt:.1f} s; rate extrapolates to the full "
+                         f"workload"}
 
     for d in dists:
         P.sk_destroy(hs[d])
@@ -332,8 +367,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16x2": "bf16x2"}[args.form], "data": "synthetic",
-            "config": {"workload": f"{args.workload} left sketch A {m}x{n} FP32 N(0,1), k={k}, "
-                                   f"S {[DIST_NAME[d] for d in dists]} Philox4x32-10 seed 7",
+            "config": {"workload": f"{args.workload} {side} sketch A {m}x{n} FP32 "
+                                   f"{'U V^T + 1e-3 E' if args.workload == 'C3' else 'N(0,1)'}, "
+                                   f"k={k}, S {[DIST_NAME[d] for d in dists]} Philox4x32-10 "
+                                   f"seed 7",
                        "m": m, "n": n, "k": k, "form": args.form,
                        "l2": f"inputs larger than L2 (A {m * n * 4 / 2**30:.2f} GiB)",
                        "parallelism": f"replicas x{world}"},
