@@ -130,6 +130,18 @@ def measured_traffic():
         return None
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest `value` over all ranks of the default process group (the
+    timing rule of the benchmark: the slowest rank defines the step time)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -276,11 +288,7 @@ def run_ours(args):
         st = P.sk_stream_status(hs[d], stream)
         if st != 0:
             raise RuntimeError(f"device status after timing: {P.status_string(st)}")
-    ms = t_start.elapsed_time(t_stop)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_stop), dev)
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
     flops_per_sketch = 2.0 * k * m * n
     flops_step = flops_per_sketch * len(dists)
@@ -331,11 +339,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e_steps):
             e2e_step()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": len(dists) * m * n * 4,
                "d2h_bytes_per_step": len(dists) * yshape[0] * yshape[1] * 4, "steps": e_steps,
