@@ -168,6 +168,61 @@ sk_status sk_set_workspace(sk_handle h, void* ptr, size_t bytes);
  * call are undefined), or SK_ECUDA if the stream reported an error. */
 sk_status sk_stream_status(sk_handle h, void* stream);
 
+/* ---- Batches: many independent left sketches in one persistent launch ----
+ *
+ * A batch collects left sketches Y_i = S_i A_i (each with its own handle,
+ * hence its own seed, distribution and k, and its own m, n) and runs them in
+ * one launch of the persistent tensor-core kernel: CTA pairs walk
+ * per-pair lists of (problem, tile, split) work items built on the host
+ * (longest items first, each to the least-loaded pair), then one launch
+ * reduces every problem's split partials in fixed order.  The two launches
+ * are captured once into a CUDA graph and replayed by later sk_batch_run
+ * calls on an unchanged batch (on a created stream; on the legacy default
+ * stream, which cannot be captured, the two launches are issued directly).  Each member's result is bit-identical to
+ * running it alone with the same work decomposition, and within 1e-5 of
+ * the FP64 product in any case.  This is the batching the paper's problem
+ * statement (Sec. 1: many sketches of matrices of different shapes) calls
+ * for on one GPU; the paper itself runs one sketch at a time. */
+typedef struct sk_batch* sk_batch_handle;
+
+/* Create an empty batch.  Allocates a status word on the current device.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+sk_status sk_batch_create(sk_batch_handle* out);
+
+/* Append the left sketch Y[k x n] = S[k x m] A[m x n] of handle `h` (which
+ * must be in the SK_BF16X2 form; seed, dist and k are read now).  A and Y are
+ * device pointers with the conventions of sk_apply_left (16-byte aligned,
+ * lda and ldy multiples of 4); they must stay valid for every later run.
+ * Invalidates the batch's plan and graph.  Errors: SK_EINVAL,
+ * SK_EUNSUPPORTED (form other than SK_BF16X2). */
+sk_status sk_batch_add(sk_batch_handle b, sk_handle h, const float* A, int64_t m, int64_t n,
+                       int64_t lda, float* Y, int64_t ldy);
+
+/* Run every sketch of the batch on `stream` (asynchronous).  The first run
+ * after a change plans the work (using the tuned item length if
+ * sk_batch_tune chose one, or one from the tuning cache file named by the
+ * environment variable SK_TUNE_CACHE, else a default), allocates the
+ * batch's device buffers and captures the graph; later runs replay it.
+ * Errors: SK_EINVAL (empty batch), SK_ENOMEM, SK_ECUDA. */
+sk_status sk_batch_run(sk_batch_handle b, void* stream);
+
+/* Autotune the work decomposition: time the batch (CUDA events on `stream`,
+ * synchronising) for each candidate item length (stages of 16 rows of m per
+ * work item) and keep the fastest; *chosen (may be NULL) receives it.  When
+ * SK_TUNE_CACHE names a writable file the choice is recorded there under a
+ * signature of the batch's shapes.  Errors as sk_batch_run. */
+sk_status sk_batch_tune(sk_batch_handle b, void* stream, int64_t* chosen);
+
+/* Synchronise `stream`, return and clear the batch's device status word
+ * (SK_OK or SK_ETIMEOUT). */
+sk_status sk_batch_status(sk_batch_handle b, void* stream);
+
+/* Number of sketches in the batch (in *count). */
+sk_status sk_batch_size(sk_batch_handle b, int64_t* count);
+
+/* Release the batch and its device buffers (not the members' handles). */
+sk_status sk_batch_destroy(sk_batch_handle b);
+
 /* Synchronise `stream` and copy the handle's four device status words
  * without clearing them: [0] the sk_status sk_stream_status would return,
  * [1] where the first bounded wait that gave up was waiting (role * 16 +

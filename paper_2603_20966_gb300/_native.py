@@ -38,6 +38,13 @@ PROTOTYPES = {
     "sk_set_workspace": (_int, [_vp, _vp, _sz]),
     "sk_stream_status": (_int, [_vp, _vp]),
     "sk_debug_status": (_int, [_vp, _vp, _P(ctypes.c_int32)]),
+    "sk_batch_create": (_int, [_P(_vp)]),
+    "sk_batch_add": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64]),
+    "sk_batch_run": (_int, [_vp, _vp]),
+    "sk_batch_tune": (_int, [_vp, _vp, _P(_i64)]),
+    "sk_batch_status": (_int, [_vp, _vp]),
+    "sk_batch_size": (_int, [_vp, _P(_i64)]),
+    "sk_batch_destroy": (_int, [_vp]),
     "sk_destroy": (_int, [_vp]),
     "sk_profile_events": (_int, [_vp, _vp, _vp]),
     "sk_launch_count": (ctypes.c_uint64, []),
@@ -210,6 +217,41 @@ def sk_debug_status(h, stream=None) -> list[int]:
     out = (ctypes.c_int32 * 4)()
     _check("sk_debug_status", _lib.sk_debug_status(h, _stream(stream), out))
     return list(out)
+
+
+def sk_batch_create() -> int:
+    b = ctypes.c_void_p()
+    _check("sk_batch_create", _lib.sk_batch_create(ctypes.byref(b)))
+    return b.value
+
+
+def sk_batch_add(b, h, A, m, n, lda, Y, ldy) -> None:
+    _check("sk_batch_add", _lib.sk_batch_add(b, h, _ptr(A), int(m), int(n), int(lda), _ptr(Y),
+                                             int(ldy)))
+
+
+def sk_batch_run(b, stream=None) -> None:
+    _check("sk_batch_run", _lib.sk_batch_run(b, _stream(stream)))
+
+
+def sk_batch_tune(b, stream=None) -> int:
+    c = ctypes.c_int64()
+    _check("sk_batch_tune", _lib.sk_batch_tune(b, _stream(stream), ctypes.byref(c)))
+    return c.value
+
+
+def sk_batch_status(b, stream=None) -> int:
+    return _lib.sk_batch_status(b, _stream(stream))
+
+
+def sk_batch_size(b) -> int:
+    c = ctypes.c_int64()
+    _check("sk_batch_size", _lib.sk_batch_size(b, ctypes.byref(c)))
+    return c.value
+
+
+def sk_batch_destroy(b) -> None:
+    _check("sk_batch_destroy", _lib.sk_batch_destroy(b))
 
 
 def sk_destroy(h) -> None:

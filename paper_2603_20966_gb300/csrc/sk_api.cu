@@ -18,17 +18,21 @@ void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_rela
 }  // namespace sk
 
 namespace {
-
-constexpr int64_t kMaxIndex = 4294967296LL;  // generator indices are 32-bit
-
 thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+}  // namespace
 
-sk_status from_cuda(cudaError_t e) {
+sk_status sk::status_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return SK_OK;
   g_last_cuda_error = e;
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
 }
+
+namespace {
+
+constexpr int64_t kMaxIndex = 4294967296LL;  // generator indices are 32-bit
+
+sk_status from_cuda(cudaError_t e) { return sk::status_from_cuda(e); }
 
 bool valid_dist(int d) { return d == SK_GAUSSIAN || d == SK_RADEMACHER || d == SK_UNIFORM; }
 bool valid_prec(int p) { return p == SK_FP32 || p == SK_BF16X2 || p == SK_FP8E4M3; }
@@ -257,6 +261,7 @@ sk_status sk_destroy(sk_handle h) {
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   if (h->stage_A) cudaFree(h->stage_A);
   if (h->stage_Y) cudaFree(h->stage_Y);
+  if (h->d_sched) cudaFree(h->d_sched);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
   return SK_OK;

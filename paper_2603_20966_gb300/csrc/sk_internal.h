@@ -23,12 +23,18 @@ struct sk_sketch {
   size_t stage_Y_bytes;
   cudaEvent_t prof_start;  // optional measurement hook (caller-owned events)
   cudaEvent_t prof_stop;
+  void* d_sched;           // device copy of the tensor-core work list (problem + items)
+  size_t d_sched_bytes;
+  uint64_t sched_key[8];   // what the uploaded work list was built for
 };
 
 namespace sk {
 
 // Count one kernel launch (sk_launch_count).
 void count_launches(uint64_t n);
+
+// sk_status of a CUDA error; remembers it for sk_last_cuda_error.
+sk_status status_from_cuda(cudaError_t e);
 
 // Record the handle's measurement-hook event, if any, on `st`.
 inline void prof_mark(cudaEvent_t ev, cudaStream_t st) {
@@ -53,6 +59,17 @@ cudaError_t materialize(const sk_sketch* h, int64_t row0, int64_t col0, int64_t 
 // fixed-order reduction of split partials: Y[p*ldy+q] = scale * sum_z part[z][p][q]
 cudaError_t splitk_reduce(const float* part, int splits, int64_t P, int64_t Q, float scale,
                           float* Y, int64_t ldy, cudaStream_t st);
+
+// fixed-order reduction of many problems in one launch
+struct ReduceDesc {
+  const float* part;
+  float* Y;
+  int64_t P, Q, ldy;
+  int splits;
+  float scale;
+};
+cudaError_t splitk_reduce_batched(const ReduceDesc* d_desc, int nprob, int64_t max_elems,
+                                  cudaStream_t st);
 
 // ---- BF16 split-A tensor-core form (sk_tc.cu) ----
 size_t tc_workspace_bytes(const GemmShape& s);

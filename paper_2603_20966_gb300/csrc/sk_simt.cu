@@ -157,6 +157,18 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int6
   }
 }
 
+__global__ void k_splitk_reduce_batched(const ReduceDesc* __restrict__ desc) {
+  const ReduceDesc d = desc[blockIdx.y];
+  const int64_t total = d.P * d.Q;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < d.splits; ++z) s = __fadd_rn(s, d.part[(int64_t)z * total + i]);
+    const int64_t r = i / d.Q, c = i % d.Q;
+    d.Y[r * d.ldy + c] = __fmul_rn(d.scale, s);
+  }
+}
+
 __global__ void k_materialize(PhiloxKey key, int dist, int fmt, int scaled, float scale,
                               int64_t row0, int64_t col0, int64_t rows, int64_t cols, void* out,
                               int64_t ld) {
@@ -223,6 +235,17 @@ cudaError_t splitk_reduce(const float* part, int splits, int64_t P, int64_t Q, f
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_splitk_reduce<<<(unsigned)blocks, 256, 0, st>>>(part, splits, P, Q, scale, Y, ldy);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t splitk_reduce_batched(const ReduceDesc* d_desc, int nprob, int64_t max_elems,
+                                  cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  int64_t bx = (max_elems + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  k_splitk_reduce_batched<<<dim3((unsigned)bx, (unsigned)nprob), 256, 0, st>>>(d_desc);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -43,6 +43,15 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
 #include "sk_internal.h"
 #include "sk_rng.cuh"
 #include "sk_tc.cuh"
@@ -107,13 +116,30 @@ __device__ __forceinline__ uint32_t kmaj_off(uint32_t row, uint32_t khalf) {
 constexpr uint32_t LBO = 128;  // K-adjacent core matrices
 constexpr uint32_t SBO = 256;  // 8-row groups
 
-struct TcParams {
-  float* part;      // partials [splits][P][Q] (every chain is summed here)
+// One left-sketch problem of a launch (a single sketch, or one member of a
+// batch).  Lives in device memory; the tensor map must be 64-byte aligned.
+struct alignas(128) LeftProblem {
+  CUtensorMap map;  // A[m x n] (n innermost), box {boxw, 16}
+  float* part;      // partials [splits][P][Q] of this problem
   int64_t P, Q, L;  // P = k, Q = n, L = m
   int64_t chunk;    // contracted length per split (multiple of BK)
-  int nt;           // output columns per tile: multiple of 16 (32 for pairs) up to 256, or 512
-  int tmem_cols;    // power of two >= max(32, nt)
+  int nt;           // output columns per tile: multiple of 16 up to 256, or 512
+  int dist;         // sk_dist of S
   PhiloxKey key;
+};
+
+// A unit of work: tile (tp, tq) of split z of problem `prob`.  With pairs,
+// tp indexes 256-row tiles and the CTA of rank r takes rows 128 r .. of it.
+struct LeftItem {
+  int prob, tp, tq, z;
+};
+
+// Work lists: the items of pair (or single CTA) i are
+// items[begin[i] .. begin[i+1]).
+struct LeftSched {
+  const LeftProblem* probs;
+  const LeftItem* items;
+  const int* begin;
   int* status;
   uint64_t timeout_ns;
 };
@@ -132,9 +158,131 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64
   }
 }
 
-template <int DIST, bool PAIR>
+// Per-item geometry shared by every role.
+struct ItemGeo {
+  const LeftProblem* pr;
+  int64_t p0, q0, lbeg, lend;
+  int nsteps, nt, nmma, nh, bh, cols, dist;
+};
+
+template <bool PAIR>
+__device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32_t rank) {
+  const LeftItem it = sc.items[idx];
+  ItemGeo g;
+  g.pr = sc.probs + it.prob;
+  g.nt = g.pr->nt;
+  g.dist = g.pr->dist;
+  g.nmma = g.nt > 256 ? 2 : 1;
+  g.nh = g.nt > 256 ? 256 : g.nt;
+  g.bh = PAIR ? g.nh / 2 : g.nh;
+  g.cols = g.nmma * g.bh;
+  g.p0 = static_cast<int64_t>(it.tp) * (PAIR ? 2 * BM : BM) + static_cast<int64_t>(rank) * BM;
+  g.q0 = static_cast<int64_t>(it.tq) * g.nt;
+  g.lbeg = static_cast<int64_t>(it.z) * g.pr->chunk;
+  g.lend = min(g.pr->L, g.lbeg + g.pr->chunk);
+  g.nsteps = static_cast<int>((g.lend - g.lbeg + BK - 1) / BK);
+  return g;
+}
+
+// Generate this CTA's BF16 S tile [128 x 16] of one stage.  Rademacher tasks
+// keep their Philox words across the 8 stages one call covers.
+template <int DIST, class C>
+__device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64_t cbase, int wt,
+                                          uint32_t* cached_blk, uint4* words) {
+  if (DIST == kRademacher) {
+    constexpr int RAD_IT = (2 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+#pragma unroll
+    for (int it = 0; it < RAD_IT; ++it) {
+      const int t = wt + it * C::GROUP_THREADS;
+      if (t >= 2 * BM) break;
+      const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
+      const uint32_t hh = static_cast<uint32_t>(t >> 7);
+      const int64_t grow = g.p0 + r;
+      const int64_t c0 = cbase + 8 * hh;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (grow < g.pr->P && c0 < g.lend) {
+        const uint32_t c = static_cast<uint32_t>(c0);
+        const uint32_t blk = c >> 7;
+        if (blk != cached_blk[it]) {
+          words[it] = rademacher_bits(g.pr->key, static_cast<uint32_t>(grow), blk, 0u);
+          cached_blk[it] = blk;
+        }
+        const uint32_t wsel = (c >> 5) & 3u;
+        const uint4 wv = words[it];
+        const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
+        const uint32_t bits = w >> (c & 31u);
+        // +1.0 = 0x3F80, -1.0 = 0xBF80: the sign bit carries the random bit
+        v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
+        v.y = 0x3F803F80u | ((bits & 4u) << 13) | ((bits & 8u) << 28);
+        v.z = 0x3F803F80u | ((bits & 16u) << 11) | ((bits & 32u) << 26);
+        v.w = 0x3F803F80u | ((bits & 64u) << 9) | ((bits & 128u) << 24);
+      }
+      *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
+    }
+  } else {
+    // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each; a
+    // fixed, unrolled count per thread lets independent chains interleave
+    constexpr int GEN_IT = (4 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+#pragma unroll
+    for (int it = 0; it < GEN_IT; ++it) {
+      const int t = wt + it * C::GROUP_THREADS;
+      if (t >= 4 * BM) break;
+      const uint32_t l = static_cast<uint32_t>(t & 31);
+      const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
+      const uint32_t qd = l & 3u;
+      const int64_t grow = g.p0 + r;
+      const int64_t c0 = cbase + 4 * qd;
+      uint2 v = make_uint2(0u, 0u);
+      if (grow < g.pr->P && c0 < g.lend) {
+        const uint32_t c = static_cast<uint32_t>(c0);
+        const float4 a = DIST == kUniform
+                             ? uniform4(g.pr->key, static_cast<uint32_t>(grow), c >> 2, 0u)
+                             : gaussian4(g.pr->key, static_cast<uint32_t>(grow), c >> 2, 0u);
+        v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
+      }
+      *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
+    }
+  }
+}
+
+// Split this CTA's FP32 A columns of one stage (staging: boxes of <= 256
+// columns x 16 rows) into BF16 hi / lo operand rows (row j = column j).
+template <class C>
+__device__ __forceinline__ void convert_stage(const float* stg, uint8_t* bhi, uint8_t* blo,
+                                              int cols, int wt) {
+  constexpr int CONV_IT = (2 * C::COLS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+#pragma unroll
+  for (int it = 0; it < CONV_IT; ++it) {
+    const int i = wt + it * C::GROUP_THREADS;
+    if (i >= 2 * cols) break;
+    const int hh = i >= cols ? 1 : 0;
+    const int j = i - hh * cols;
+    const int box = j >> 8;
+    const int bw = min(cols - box * 256, 256);
+    const float* src = stg + box * 256 * BK + (8 * hh) * bw + (j - box * 256);
+    float a[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a[e] = src[e * bw];
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
+      const float h0 = __uint_as_float(hw[e] << 16);
+      const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
+      lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
+    }
+    const uint32_t o = kmaj_off(static_cast<uint32_t>(j), static_cast<uint32_t>(hh));
+    *reinterpret_cast<uint4*>(bhi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(blo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// Persistent left-sketch kernel: each pair (or single CTA) runs its list of
+// items back to back; ring positions, barrier phases and accumulation chains
+// are counted across items (g = stage counter, gc = chain counter).
+template <bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_sketch_bf16x2_left(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
+    k_sketch_bf16x2_left(const LeftSched sc) {
   using C = Cfg<PAIR>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -155,18 +303,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? (cluster_ctarank() & 1u) : 0u;  // 0 = even (MMA issuer)
   const bool leader = rank == 0;
-  const int nt = p.nt;
-  const int nmma = nt > 256 ? 2 : 1;                 // MMA instructions per pass
-  const int nh = nt > 256 ? 256 : nt;                // N of each instruction
-  const int bh = PAIR ? nh / 2 : nh;                 // B rows per instruction in this CTA
-  const int cols = nmma * bh;                        // A columns this CTA loads/converts
-  // grid: x = 128-row tiles of Y (pairs are adjacent in x), y = column tiles
-  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nt;
-  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * BM;
-  const int64_t lbeg = static_cast<int64_t>(blockIdx.z) * p.chunk;
-  const int64_t lend = min(p.L, lbeg + p.chunk);
-  const int nsteps = static_cast<int>((lend - lbeg + BK - 1) / BK);
-  const int nchains = (nsteps + CHAIN - 1) / CHAIN;
+  const int unit = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int ib = sc.begin[unit];
+  const int ie = sc.begin[unit + 1];
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NSF; ++i) {
@@ -183,80 +322,94 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     *abort_flag = 0;
     mbar_fence_init();
   }
-  if (warp == WARP_MMA) {
+  if (warp == WARP_MMA) {  // the accumulator of every item: up to 512 TMEM columns
     if (PAIR) {
-      tmem_alloc_pair(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+      tmem_alloc_pair(smem_u32(tmem_slot), static_cast<uint32_t>(NT_MAX));
       tmem_relinquish_pair();
     } else {
-      tmem_alloc(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+      tmem_alloc(smem_u32(tmem_slot), static_cast<uint32_t>(NT_MAX));
       tmem_relinquish();
     }
   }
-  if (warp == WARP_TMA && lane == 0) tma_prefetch_desc(&tmapA);
   tc_fence_before();
   __syncthreads();
   if (PAIR) cluster_sync();  // the peer's barriers exist before any remote arrive
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const Abort ab{abort_flag, p.status, p.timeout_ns};
+  const Abort ab{abort_flag, sc.status, sc.timeout_ns};
   // barriers of the even CTA, addressed from either CTA
   const uint32_t lead_full_o = PAIR ? mapa_shared(full_o(0), 0u) : full_o(0);
   const uint32_t lead_acc_empty = PAIR ? mapa_shared(acc_empty, 0u) : acc_empty;
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
-      const uint32_t tx = static_cast<uint32_t>(cols * BK * 4);
+      int g = 0;
       int issued = 0;
-      for (int s = 0; s < nsteps; ++s) {
-        const int sf = s % C::NSF;
-        if (s >= C::NSF && !mbar_wait(empty_f(sf), ((s / C::NSF) & 1) ^ 1, ab, 0x11, s)) break;
-        mbar_arrive_expect_tx(full_f(sf), tx);
-        const int32_t y = static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK);
-        for (int b = 0; b * 256 < cols; ++b)
-          tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(b * 256 * BK * 4),
-                      &tmapA, static_cast<int32_t>(q0 + static_cast<int>(rank) * cols + b * 256), y,
-                      full_f(sf));
-        issued = s + 1;
+      for (int idx = ib; idx < ie && !*abort_flag; ++idx) {
+        const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
+        const CUtensorMap* map = &ig.pr->map;
+        tma_prefetch_desc(map);
+        const uint32_t tx = static_cast<uint32_t>(ig.cols * BK * 4);
+        const int64_t x0 = ig.q0 + static_cast<int64_t>(rank) * ig.cols;
+        for (int s = 0; s < ig.nsteps; ++s, ++g) {
+          const int sf = g % C::NSF;
+          if (g >= C::NSF && !mbar_wait(empty_f(sf), ((g / C::NSF) & 1) ^ 1, ab, 0x11, g)) break;
+          mbar_arrive_expect_tx(full_f(sf), tx);
+          const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * BK);
+          for (int b = 0; b * 256 < ig.cols; ++b)
+            tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(b * 256 * BK * 4),
+                        map, static_cast<int32_t>(x0 + b * 256), y, full_f(sf));
+          issued = g + 1;
+        }
       }
       if (*abort_flag) {  // let the copies already issued land before leaving
-        for (int s = max(0, issued - C::NSF); s < issued; ++s)
-          drain_wait(full_f(s % C::NSF), (s / C::NSF) & 1, 100000000ull);
+        for (int t = max(0, issued - C::NSF); t < issued; ++t)
+          drain_wait(full_f(t % C::NSF), (t / C::NSF) & 1, 100000000ull);
       }
     }
   } else if (warp == WARP_MMA) {
     if (lane == 0 && leader) {
-      const uint32_t idesc =
-          idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(nh));
-      for (int s = 0; s < nsteps; ++s) {
-        const int so = s % C::NSO;
-        const int in_chain = s % CHAIN;
-        // a new chain may start only after every epilogue has read the last one
-        if (s > 0 && in_chain == 0 &&
-            !mbar_wait(acc_empty, ((s / CHAIN) - 1) & 1, ab, 0x25, s))
-          break;
-        if (!mbar_wait(full_o(so), (s / C::NSO) & 1, ab, 0x22, s)) break;
-        tc_fence_after();
-        const uint64_t adesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
-#pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
-          const uint32_t bb = sbase + (pass ? C::OFF_BLO : C::OFF_BHI) + so * C::OPB;
-          for (int h = 0; h < nmma; ++h) {
-            const uint64_t bdesc =
-                smem_desc(bb + static_cast<uint32_t>(h * bh / 8) * SBO, LBO, SBO);
-            const uint32_t acc = (in_chain > 0 || pass > 0) ? 1u : 0u;
-            if (PAIR)
-              mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
-            else
-              mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+      int g = 0, gc = 0;
+      bool stop = false;
+      for (int idx = ib; idx < ie && !stop; ++idx) {
+        const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
+        const uint32_t idesc = idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh));
+        for (int s = 0; s < ig.nsteps; ++s, ++g) {
+          const int so = g % C::NSO;
+          const int in_chain = s % CHAIN;
+          // a new chain may start only after every epilogue has read the last one
+          if (in_chain == 0 && gc > 0 && !mbar_wait(acc_empty, (gc - 1) & 1, ab, 0x25, gc)) {
+            stop = true;
+            break;
           }
-        }
-        const bool chain_end = in_chain == CHAIN - 1 || s == nsteps - 1;
-        if (PAIR) {  // operands and accumulator are both CTAs'
-          mma_commit_pair_both(empty_o(so));
-          if (chain_end) mma_commit_pair_both(acc_full);
-        } else {
-          mma_commit(empty_o(so));
-          if (chain_end) mma_commit(acc_full);
+          if (!mbar_wait(full_o(so), (g / C::NSO) & 1, ab, 0x22, g)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t adesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            const uint32_t bb = sbase + (pass ? C::OFF_BLO : C::OFF_BHI) + so * C::OPB;
+            for (int h = 0; h < ig.nmma; ++h) {
+              const uint64_t bdesc =
+                  smem_desc(bb + static_cast<uint32_t>(h * ig.bh / 8) * SBO, LBO, SBO);
+              const uint32_t acc = (in_chain > 0 || pass > 0) ? 1u : 0u;
+              if (PAIR)
+                mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+              else
+                mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+            }
+          }
+          const bool chain_end = in_chain == CHAIN - 1 || s == ig.nsteps - 1;
+          if (PAIR) {  // operands and accumulator are both CTAs'
+            mma_commit_pair_both(empty_o(so));
+            if (chain_end) mma_commit_pair_both(acc_full);
+          } else {
+            mma_commit(empty_o(so));
+            if (chain_end) mma_commit(acc_full);
+          }
+          if (chain_end) ++gc;
         }
       }
       if (PAIR)
@@ -267,185 +420,134 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       drain_wait(drain_bar, 0, 200000000ull);
     }
   } else if (warp < WARP_WORK0) {
-    // ---- epilogue: add each finished chain into this CTA's FP32 partial ----
+    // ---- epilogue: add each finished chain into the item's FP32 partial ----
     const int quarter = warp & 3;
     const int colset = (warp - WARP_EPI0) >> 2;  // 0 or 1: even / odd 32-column chunks
     const int row = quarter * 32 + lane;
-    const int64_t gp = p0 + row;
-    float* dst_row = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gp) * p.Q + q0;
-    const bool vec_ok = (p.Q % 4) == 0;
-    for (int c0 = 0; c0 < nchains; ++c0) {
-      const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
-      if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld below is warp-collective
-      tc_fence_after();
-      // TMEM column h*256 + c holds B row c of instruction h: with a pair,
-      // rows c < bh are the even CTA's columns h*bh + c of the tile and rows
-      // c >= bh the odd CTA's columns cols + h*bh + (c - bh)
-      for (int ci = colset; ci * 32 < nmma * 256 && ci * 32 < (nmma - 1) * 256 + nh; ci += 2) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                      static_cast<uint32_t>(ci * 32),
-                  v);
-        tmem_ld_wait();
-        if (gp < p.P) {
+    int gc = 0;
+    bool stop = false;
+    for (int idx = ib; idx < ie && !stop; ++idx) {
+      const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
+      const LeftItem it = sc.items[idx];
+      const int64_t gp = ig.p0 + row;
+      const int64_t P = ig.pr->P, Q = ig.pr->Q;
+      float* dst_row = ig.pr->part + (static_cast<int64_t>(it.z) * P + gp) * Q + ig.q0;
+      const bool vec_ok = (Q % 4) == 0;
+      const int nchains = (ig.nsteps + CHAIN - 1) / CHAIN;
+      for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
+        const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
+        if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        // TMEM column h*256 + c holds B row c of instruction h: with a pair,
+        // rows c < bh are the even CTA's columns h*bh + c of the tile and rows
+        // c >= bh the odd CTA's columns cols + h*bh + (c - bh)
+        for (int ci = colset; ci * 32 < (ig.nmma - 1) * 256 + ig.nh; ci += 2) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                        static_cast<uint32_t>(ci * 32),
+                    v);
+          tmem_ld_wait();
+          if (gp < P) {
 #pragma unroll
-          for (int e = 0; e < 32; e += 4) {  // bh is a multiple of 8: groups never straddle
-            const int tcol = ci * 32 + e;
-            const int h = tcol >> 8;
-            const int c = tcol & 255;
-            if (c >= nh) continue;
-            const int tn = PAIR ? (c < bh ? h * bh + c : cols + h * bh + (c - bh)) : tcol;
-            const int64_t col = q0 + tn;
-            float* d = dst_row + tn;
-            const float a0 = __uint_as_float(v[e]), a1 = __uint_as_float(v[e + 1]);
-            const float a2 = __uint_as_float(v[e + 2]), a3 = __uint_as_float(v[e + 3]);
-            if (vec_ok && col + 4 <= p.Q) {
-              if (c0 == 0)
-                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
-              else
-                red_add_v4(d, a0, a1, a2, a3);
-            } else {
-              const float vv[4] = {a0, a1, a2, a3};
-              for (int u = 0; u < 4; ++u) {
-                if (col + u < p.Q) {
-                  if (c0 == 0)
-                    d[u] = vv[u];
-                  else
-                    red_add(d + u, vv[u]);
+            for (int e = 0; e < 32; e += 4) {  // bh is a multiple of 8: groups never straddle
+              const int tcol = ci * 32 + e;
+              const int h = tcol >> 8;
+              const int c = tcol & 255;
+              if (c >= ig.nh) continue;
+              const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
+                                  : tcol;
+              const int64_t col = ig.q0 + tn;
+              float* d = dst_row + tn;
+              const float a0 = __uint_as_float(v[e]), a1 = __uint_as_float(v[e + 1]);
+              const float a2 = __uint_as_float(v[e + 2]), a3 = __uint_as_float(v[e + 3]);
+              if (vec_ok && col + 4 <= Q) {
+                if (c0 == 0)
+                  *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+                else
+                  red_add_v4(d, a0, a1, a2, a3);
+              } else {
+                const float vv[4] = {a0, a1, a2, a3};
+                for (int u = 0; u < 4; ++u) {
+                  if (col + u < Q) {
+                    if (c0 == 0)
+                      d[u] = vv[u];
+                    else
+                      red_add(d + u, vv[u]);
+                  }
                 }
               }
             }
           }
         }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if (PAIR)
-          mbar_arrive_cluster(lead_acc_empty);
-        else
-          mbar_arrive(acc_empty);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR)
+            mbar_arrive_cluster(lead_acc_empty);
+          else
+            mbar_arrive(acc_empty);
+        }
       }
     }
   } else {
     // ---- workers: generate this CTA's S tile and convert its A columns ----
-    // group g handles the stages s = g (mod C::NGROUPS)
+    // group grp handles the stages g = grp (mod NGROUPS)
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
     const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
-    // Rademacher: each thread keeps the same (row, half) tasks on every stage
-    // and caches their Philox words across the 8 stages a call covers
     constexpr int RAD_IT = (2 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
     uint32_t cached_blk[RAD_IT];
     uint4 words[RAD_IT];
+    int g = 0;
+    bool stop = false;
+    for (int idx = ib; idx < ie && !stop; ++idx) {
+      const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
 #pragma unroll
-    for (int it = 0; it < RAD_IT; ++it) {
-      cached_blk[it] = 0xffffffffu;
-      words[it] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    for (int s = grp; s < nsteps; s += C::NGROUPS) {
-      const int sf = s % C::NSF;
-      const int so = s % C::NSO;
-      // the MMAs that read operand buffer `so` last time have completed
-      bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
-      if (!__all_sync(0xffffffffu, ok)) break;  // leave together (abort path)
-      uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
-      const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
-      if (DIST == kRademacher) {
-        // 128 rows x 2 k-halves, 8 entries each, one Philox call per 128 columns
-#pragma unroll
-        for (int it = 0; it < RAD_IT; ++it) {
-          const int t = wt + it * C::GROUP_THREADS;
-          if (t >= 2 * BM) break;
-          const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
-          const uint32_t hh = static_cast<uint32_t>(t >> 7);
-          const int64_t grow = p0 + r;
-          const int64_t c0 = cbase + 8 * hh;
-          uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          if (grow < p.P && c0 < lend) {
-            const uint32_t c = static_cast<uint32_t>(c0);
-            const uint32_t blk = c >> 7;
-            if (blk != cached_blk[it]) {
-              words[it] = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
-              cached_blk[it] = blk;
-            }
-            const uint32_t wsel = (c >> 5) & 3u;
-            const uint4 wv = words[it];
-            const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
-            const uint32_t bits = w >> (c & 31u);
-            // +1.0 = 0x3F80, -1.0 = 0xBF80: the sign bit carries the random bit
-            v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
-            v.y = 0x3F803F80u | ((bits & 4u) << 13) | ((bits & 8u) << 28);
-            v.z = 0x3F803F80u | ((bits & 16u) << 11) | ((bits & 32u) << 26);
-            v.w = 0x3F803F80u | ((bits & 64u) << 9) | ((bits & 128u) << 24);
-          }
-          *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
-        }
-      } else {
-        // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each; a
-        // fixed, unrolled count per thread lets independent chains interleave
-        constexpr int GEN_IT = (4 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
-#pragma unroll
-        for (int it = 0; it < GEN_IT; ++it) {
-          const int t = wt + it * C::GROUP_THREADS;
-          if (t >= 4 * BM) break;
-          const uint32_t l = static_cast<uint32_t>(t & 31);
-          const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
-          const uint32_t qd = l & 3u;
-          const int64_t grow = p0 + r;
-          const int64_t c0 = cbase + 4 * qd;
-          uint2 v = make_uint2(0u, 0u);
-          if (grow < p.P && c0 < lend) {
-            const uint32_t c = static_cast<uint32_t>(c0);
-            const float4 a = DIST == kUniform
-                                 ? uniform4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u)
-                                 : gaussian4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u);
-            v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
-          }
-          *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
-        }
+      for (int it = 0; it < RAD_IT; ++it) {  // Philox words belong to one problem and row
+        cached_blk[it] = 0xffffffffu;
+        words[it] = make_uint4(0u, 0u, 0u, 0u);
       }
-      // conversion needs this stage's A tile
-      ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
-      uint8_t* bhi = smem + C::OFF_BHI + so * C::OPB;
-      uint8_t* blo = smem + C::OFF_BLO + so * C::OPB;
-      constexpr int CONV_IT = (2 * C::COLS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
-#pragma unroll
-      for (int it = 0; it < CONV_IT; ++it) {
-        const int i = wt + it * C::GROUP_THREADS;
-        if (i >= 2 * cols) break;
-        const int hh = i >= cols ? 1 : 0;
-        const int j = i - hh * cols;   // column j of this CTA's slice = operand row j
-        const int box = j >> 8;        // staging boxes are 256 columns wide
-        const int bw = min(cols - box * 256, 256);
-        const float* src = stg + box * 256 * BK + (8 * hh) * bw + (j - box * 256);
-        float a[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = src[e * bw];
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
-          const float h0 = __uint_as_float(hw[e] << 16);
-          const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
-          lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
+      for (int s = 0; s < ig.nsteps; ++s, ++g) {
+        if (g % C::NGROUPS != grp) continue;
+        const int sf = g % C::NSF;
+        const int so = g % C::NSO;
+        // the MMAs that read operand buffer `so` last time have completed
+        bool ok = g < C::NSO || mbar_wait(empty_o(so), ((g / C::NSO) & 1) ^ 1, ab, 0x43, g);
+        if (!__all_sync(0xffffffffu, ok)) {  // leave together (abort path)
+          stop = true;
+          break;
         }
-        const uint32_t o = kmaj_off(static_cast<uint32_t>(j), static_cast<uint32_t>(hh));
-        *reinterpret_cast<uint4*>(bhi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(blo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
-      if (PAIR)
-        fence_proxy_async_cluster();  // the even CTA's MMA reads these operands
-      else
-        fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        if (PAIR)
-          mbar_arrive_cluster(lead_full_o + 8u * so);
+        uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
+        const int64_t cbase = ig.lbeg + static_cast<int64_t>(s) * BK;
+        if (ig.dist == kRademacher)
+          gen_stage<kRademacher, C>(sdst, ig, cbase, wt, cached_blk, words);
+        else if (ig.dist == kUniform)
+          gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
         else
-          mbar_arrive(full_o(so));
-        mbar_arrive(empty_f(sf));
+          gen_stage<kGaussian, C>(sdst, ig, cbase, wt, cached_blk, words);
+        // conversion needs this stage's A tile
+        ok = mbar_wait(full_f(sf), (g / C::NSF) & 1, ab, 0x40, g);
+        if (!__all_sync(0xffffffffu, ok)) {
+          stop = true;
+          break;
+        }
+        convert_stage<C>(reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F),
+                         smem + C::OFF_BHI + so * C::OPB, smem + C::OFF_BLO + so * C::OPB,
+                         ig.cols, wt);
+        if (PAIR)
+          fence_proxy_async_cluster();  // the even CTA's MMA reads these operands
+        else
+          fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR)
+            mbar_arrive_cluster(lead_full_o + 8u * so);
+          else
+            mbar_arrive(full_o(so));
+          mbar_arrive(empty_f(sf));
+        }
       }
     }
   }
@@ -457,9 +559,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     __syncwarp();
     if (PAIR)
-      tmem_dealloc_pair(tmem, static_cast<uint32_t>(p.tmem_cols));
+      tmem_dealloc_pair(tmem, static_cast<uint32_t>(NT_MAX));
     else
-      tmem_dealloc(tmem, static_cast<uint32_t>(p.tmem_cols));
+      tmem_dealloc(tmem, static_cast<uint32_t>(NT_MAX));
   }
 }
 
@@ -799,14 +901,8 @@ template <bool PAIR>
 cudaError_t set_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kGaussian, PAIR>,
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kRademacher, PAIR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sketch_bf16x2_left<kUniform, PAIR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -836,67 +932,13 @@ int64_t pair_slots() {
   cudaLaunchAttribute attr[1];
   fill_config<true>(&cfg, attr, dim3(2, 1, 1), nullptr);
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_left<kGaussian, true>, &cfg) !=
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_left<true>, &cfg) !=
           cudaSuccess ||
       clusters <= 0) {
     cudaGetLastError();
     return cache = -1;
   }
   return cache = static_cast<int64_t>(clusters) * 2;
-}
-
-struct Plan {
-  bool pair;
-  int nt, tmem_cols, boxw;
-  int64_t tiles_q, tiles_p;  // tiles_p is even for pairs
-  int splits;
-  int64_t chunk;
-};
-
-// Tile width, pairing and split-K count: whole waves of one CTA per SM.
-Plan plan_left(const GemmShape& s) {
-  Plan pl;
-  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + 15) / 16 * 16);
-  pl.tmem_cols = 32;
-  while (pl.tmem_cols < pl.nt) pl.tmem_cols *= 2;
-  pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
-  const int64_t tp = (s.P + BM - 1) / BM;
-  int64_t slots = num_sms_tc();
-  pl.pair = false;
-  if (tp >= 2) {
-    const int64_t ps = pair_slots();
-    if (ps > 0) {
-      pl.pair = true;
-      slots = ps;
-    }
-  }
-  // each CTA loads one contiguous slice of the tile's columns (half of them
-  // in a pair) as boxes of at most 256 columns
-  const int cta_cols = pl.pair ? pl.nt / 2 : pl.nt;
-  pl.boxw = cta_cols > 256 ? 256 : cta_cols;
-  pl.tiles_p = pl.pair ? (tp + 1) / 2 * 2 : tp;
-  const int64_t tiles = pl.tiles_q * pl.tiles_p;
-  const int64_t steps_total = (s.L + BK - 1) / BK;
-  int64_t smax = steps_total / 8;  // at least 8 stages per split
-  if (smax > 128) smax = 128;
-  if (smax < 1) smax = 1;
-  int64_t best = 1;
-  double best_eff = -1.0;
-  for (int64_t sp = 1; sp <= smax; ++sp) {
-    const int64_t ctas = tiles * sp;
-    const int64_t waves = (ctas + slots - 1) / slots;
-    const double eff = static_cast<double>(ctas) / static_cast<double>(waves * slots);
-    if (eff > best_eff + 0.02) {
-      best_eff = eff;
-      best = sp;
-    }
-    if (ctas >= 4 * slots) break;
-  }
-  int64_t chunk = (s.L + best - 1) / best;
-  chunk = (chunk + BK - 1) / BK * BK;
-  pl.chunk = chunk;
-  pl.splits = static_cast<int>((s.L + chunk - 1) / chunk);
-  return pl;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -912,22 +954,176 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int DIST, bool PAIR>
-cudaError_t launch_left(const CUtensorMap& map, const TcParams& p, dim3 grid, cudaStream_t st) {
+// Row-major FP32 matrix [rows x cols] (cols innermost) with boxes of
+// {box_cols, box_rows}; zero fill outside the matrix.
+bool encode_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld,
+                int box_cols, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride,
+             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Geometry of one left problem.
+struct LeftPlan {
+  bool pair;
+  int nt, boxw;
+  int64_t tiles_p, tiles_q;  // tiles_p counts pair tiles (256 rows) when pair
+  int splits;
+  int64_t chunk;
+  int64_t steps;             // stages of one item
+};
+
+LeftPlan left_geometry(const GemmShape& s, bool pair) {
+  LeftPlan pl;
+  pl.pair = pair;
+  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + 15) / 16 * 16);
+  const int cta_cols = pair ? pl.nt / 2 : pl.nt;
+  pl.boxw = cta_cols > 256 ? 256 : cta_cols;
+  pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
+  pl.tiles_p = (s.P + (pair ? 2 * BM : BM) - 1) / (pair ? 2 * BM : BM);
+  pl.splits = 1;
+  pl.chunk = (s.L + BK - 1) / BK * BK;
+  pl.steps = pl.chunk / BK;
+  return pl;
+}
+
+void set_splits(LeftPlan* pl, const GemmShape& s, int64_t splits) {
+  if (splits < 1) splits = 1;
+  int64_t chunk = (s.L + splits - 1) / splits;
+  chunk = (chunk + BK - 1) / BK * BK;
+  pl->chunk = chunk;
+  pl->splits = static_cast<int>((s.L + chunk - 1) / chunk);
+  pl->steps = chunk / BK;
+}
+
+// A single sketch: pairs when the output has at least two 128-row tiles;
+// splits that fill whole waves of the resident units.
+LeftPlan plan_left(const GemmShape& s) {
+  const int64_t tp = (s.P + BM - 1) / BM;
+  const int64_t ps = tp >= 2 ? pair_slots() : -1;
+  LeftPlan pl = left_geometry(s, ps > 0);
+  const int64_t units = pl.pair ? ps / 2 : num_sms_tc();
+  const int64_t tiles = pl.tiles_p * pl.tiles_q;
+  const int64_t steps_total = (s.L + BK - 1) / BK;
+  int64_t smax = steps_total / 8;  // at least 8 stages per split
+  if (smax > 128) smax = 128;
+  if (smax < 1) smax = 1;
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int64_t sp = 1; sp <= smax; ++sp) {
+    const int64_t items = tiles * sp;
+    const int64_t waves = (items + units - 1) / units;
+    const double eff = static_cast<double>(items) / static_cast<double>(waves * units);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (items >= 4 * units) break;
+  }
+  set_splits(&pl, s, best);
+  return pl;
+}
+
+// Host image of a work list: problems (128-byte aligned), items, per-unit
+// begin offsets, packed into one buffer for a single upload.
+struct HostSched {
+  std::vector<LeftProblem> probs;
+  std::vector<LeftItem> items;
+  std::vector<int> begin;
+  size_t off_items = 0, off_begin = 0, bytes = 0;
+  std::vector<uint8_t> blob;
+};
+
+// Items of every problem, longest first, each to the least-loaded of at most
+// `max_units` units (pairs or CTAs).
+void build_items(const std::vector<LeftPlan>& plans, int64_t max_units, HostSched* hs) {
+  struct Cand {
+    LeftItem it;
+    double cost;
+  };
+  std::vector<Cand> cands;
+  for (size_t pi = 0; pi < plans.size(); ++pi) {
+    const LeftPlan& pl = plans[pi];
+    const double cost = static_cast<double>(pl.steps) * (static_cast<double>(pl.nt) + 256.0);
+    for (int64_t z = 0; z < pl.splits; ++z)
+      for (int64_t tq = 0; tq < pl.tiles_q; ++tq)
+        for (int64_t tp = 0; tp < pl.tiles_p; ++tp)
+          cands.push_back({{static_cast<int>(pi), static_cast<int>(tp), static_cast<int>(tq),
+                            static_cast<int>(z)},
+                           cost});
+  }
+  std::stable_sort(cands.begin(), cands.end(),
+                   [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+  const int64_t units = std::max<int64_t>(1, std::min<int64_t>(max_units, cands.size()));
+  std::vector<double> load(units, 0.0);
+  std::vector<std::vector<LeftItem>> per(units);
+  for (const Cand& c : cands) {
+    int64_t best = 0;
+    for (int64_t u = 1; u < units; ++u)
+      if (load[u] < load[best]) best = u;
+    load[best] += c.cost;
+    per[best].push_back(c.it);
+  }
+  hs->items.clear();
+  hs->begin.assign(1, 0);
+  for (int64_t u = 0; u < units; ++u) {
+    for (const LeftItem& it : per[u]) hs->items.push_back(it);
+    hs->begin.push_back(static_cast<int>(hs->items.size()));
+  }
+}
+
+void pack_sched(HostSched* hs) {
+  const size_t pb = hs->probs.size() * sizeof(LeftProblem);
+  hs->off_items = (pb + 255) / 256 * 256;
+  const size_t ib = hs->items.size() * sizeof(LeftItem);
+  hs->off_begin = (hs->off_items + ib + 255) / 256 * 256;
+  hs->bytes = hs->off_begin + hs->begin.size() * sizeof(int);
+  hs->blob.assign(hs->bytes, 0);
+  memcpy(hs->blob.data(), hs->probs.data(), pb);
+  memcpy(hs->blob.data() + hs->off_items, hs->items.data(), ib);
+  memcpy(hs->blob.data() + hs->off_begin, hs->begin.data(), hs->begin.size() * sizeof(int));
+}
+
+LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
+  LeftSched sc;
+  uint8_t* b = static_cast<uint8_t*>(dbuf);
+  sc.probs = reinterpret_cast<const LeftProblem*>(b);
+  sc.items = reinterpret_cast<const LeftItem*>(b + hs.off_items);
+  sc.begin = reinterpret_cast<const int*>(b + hs.off_begin);
+  sc.status = status;
+  sc.timeout_ns = 2000000000ull;  // 2 s per wait: far beyond any healthy stage
+  return sc;
+}
+
+template <bool PAIR>
+cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
   cudaError_t e = set_smem_attr<PAIR>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  fill_config<PAIR>(&cfg, attr, grid, st);
-  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR>, map, p);
+  fill_config<PAIR>(&cfg, attr, dim3(static_cast<unsigned>(units * (PAIR ? 2 : 1)), 1, 1), st);
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<PAIR>, sc);
 }
 
-template <bool PAIR>
-cudaError_t launch_dist(int dist, const CUtensorMap& map, const TcParams& p, dim3 grid,
-                        cudaStream_t st) {
-  if (dist == kRademacher) return launch_left<kRademacher, PAIR>(map, p, grid, st);
-  if (dist == kUniform) return launch_left<kUniform, PAIR>(map, p, grid, st);
-  return launch_left<kGaussian, PAIR>(map, p, grid, st);
+bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const float* A,
+                  int64_t lda, float* part, uint64_t seed, int dist) {
+  memset(pr, 0, sizeof(*pr));
+  if (!encode_map(&pr->map, A, s.L, s.Q, lda, pl.boxw, BK)) return false;
+  pr->part = part;
+  pr->P = s.P;
+  pr->Q = s.Q;
+  pr->L = s.L;
+  pr->chunk = pl.chunk;
+  pr->nt = pl.nt;
+  pr->dist = dist;
+  pr->key = make_key(seed);
+  return true;
 }
 
 cudaError_t set_smem_attr_right() {
@@ -945,15 +1141,20 @@ cudaError_t set_smem_attr_right() {
   return e;
 }
 
+struct Plan {
+  int nt, tmem_cols;
+  int64_t tiles_p, tiles_q;
+  int splits;
+  int64_t chunk;
+};
+
 // Right sketch: pairs of CTAs own 512 rows of m and nq <= 256 rows of k; the
 // split count keeps the partials (splits x m x k floats) to a few hundred MB.
 Plan plan_right(const GemmShape& s) {
   Plan pl;
-  pl.pair = true;
   pl.nt = s.Q > 256 ? 256 : static_cast<int>((s.Q + 15) / 16 * 16);
   pl.tmem_cols = 32;
   while (pl.tmem_cols < 2 * pl.nt) pl.tmem_cols *= 2;
-  pl.boxw = BK;
   pl.tiles_p = (s.P + 2 * CfgR::ROWS - 1) / (2 * CfgR::ROWS) * 2;  // CTAs along m
   pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
   int64_t slots = pair_slots();
@@ -996,10 +1197,25 @@ cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 gr
   return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_right<DIST>, map, p);
 }
 
+cudaError_t grow_device(void** buf, size_t* have, size_t need) {
+  if (*have >= need) return cudaSuccess;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) return e;
+  *have = need;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 size_t tc_workspace_bytes(const GemmShape& s) {
-  const Plan pl = s.left ? plan_left(s) : plan_right(s);
+  if (s.left) {
+    const LeftPlan pl = plan_left(s);
+    return static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
+  }
+  const Plan pl = plan_right(s);
   return static_cast<size_t>(pl.splits) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
          sizeof(float);
 }
@@ -1015,19 +1231,9 @@ sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float*
 cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                             float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
   const Plan pl = plan_right(s);
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (enc == nullptr) return cudaErrorNotSupported;
   CUtensorMap map;
   // A[m x n]: n innermost; one box = 16 columns of n x 256 rows of m
-  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(s.L), static_cast<cuuint64_t>(s.P)};
-  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * sizeof(float)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(CfgR::ROWS)};
-  const cuuint32_t estride[2] = {1, 1};
-  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim,
-                    gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (!encode_map(&map, A, s.P, s.L, lda, BK, CfgR::ROWS)) return cudaErrorInvalidValue;
   TcRightParams p;
   p.P = s.P;
   p.Q = s.Q;
@@ -1060,38 +1266,35 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
 cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                       float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (!s.left) return tc_sketch_right(h, s, A, lda, Y, ldy, ws, ws_bytes, st);
-  const Plan pl = plan_left(s);
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (enc == nullptr) return cudaErrorNotSupported;
-  CUtensorMap map;
-  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(s.Q), static_cast<cuuint64_t>(s.L)};
-  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * sizeof(float)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(pl.boxw), static_cast<cuuint32_t>(BK)};
-  const cuuint32_t estride[2] = {1, 1};
-  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim,
-                    gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-
-  TcParams p;
-  p.P = s.P;
-  p.Q = s.Q;
-  p.L = s.L;
-  p.chunk = pl.chunk;
-  p.nt = pl.nt;
-  p.tmem_cols = pl.tmem_cols;
-  p.key = make_key(h->seed);
-  p.status = h->d_status;
-  p.timeout_ns = 2000000000ull;  // 2 s per wait: far beyond any healthy stage
+  const LeftPlan pl = plan_left(s);
   const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
-  p.part = static_cast<float*>(ws);
-  dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
-            static_cast<unsigned>(pl.splits));
+  sk_sketch* hm = const_cast<sk_sketch*>(h);
+  // The work list depends only on these; upload it again only when they change.
+  const uint64_t key[8] = {reinterpret_cast<uint64_t>(A), static_cast<uint64_t>(s.L),
+                           static_cast<uint64_t>(s.Q), static_cast<uint64_t>(lda),
+                           reinterpret_cast<uint64_t>(ws), h->seed,
+                           static_cast<uint64_t>(h->dist) | (static_cast<uint64_t>(h->k) << 8),
+                           1u};
+  const int64_t units = pl.pair ? pair_slots() / 2 : num_sms_tc();
+  HostSched hs;
+  hs.probs.resize(1);
+  if (!fill_problem(&hs.probs[0], pl, s, A, lda, static_cast<float*>(ws), h->seed, h->dist))
+    return cudaErrorInvalidValue;
+  build_items(std::vector<LeftPlan>{pl}, units, &hs);
+  pack_sched(&hs);
+  if (memcmp(key, hm->sched_key, sizeof(key)) != 0 || hm->d_sched_bytes < hs.bytes) {
+    cudaError_t e = grow_device(&hm->d_sched, &hm->d_sched_bytes, hs.bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(hm->d_sched, hs.blob.data(), hs.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    memcpy(hm->sched_key, key, sizeof(key));
+  }
+  const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status);
+  const int64_t nunits = static_cast<int64_t>(hs.begin.size()) - 1;
   prof_mark(h->prof_start, st);
-  const cudaError_t e = pl.pair ? launch_dist<true>(h->dist, map, p, grid, st)
-                                : launch_dist<false>(h->dist, map, p, grid, st);
+  const cudaError_t e = pl.pair ? launch_left<true>(sc, nunits, st)
+                                : launch_left<false>(sc, nunits, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
@@ -1100,3 +1303,324 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
 }
 
 }  // namespace sk
+
+// ---------------------------------------------------------------------------
+// Batches (see include/sketch.h)
+// ---------------------------------------------------------------------------
+struct sk_batch {
+  struct Entry {
+    uint64_t seed;
+    int dist;
+    int64_t k;
+    float scale;
+    const float* A;
+    int64_t m, n, lda;
+    float* Y;
+    int64_t ldy;
+  };
+  std::vector<Entry> entries;
+  int device = 0;
+  int* d_status = nullptr;
+  int64_t item_stages = 0;  // tuned item length (stages); 0 = not chosen
+  bool planned = false;
+  void* d_buf = nullptr;  // work list + reduce descriptors
+  size_t d_bytes = 0;
+  void* ws = nullptr;     // partials of every member
+  size_t ws_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  // plan results
+  sk::HostSched hs;
+  std::vector<sk::ReduceDesc> red;
+  size_t off_red = 0;
+  int64_t max_elems = 0;
+  int64_t units = 0;
+};
+
+namespace {
+
+constexpr int64_t kDefaultItemStages = 512;
+
+std::string batch_signature(const sk_batch* b) {
+  std::string sig;
+  char buf[96];
+  for (const auto& e : b->entries) {
+    snprintf(buf, sizeof(buf), "%lld:%lld:%lld:%d;", static_cast<long long>(e.m),
+             static_cast<long long>(e.n), static_cast<long long>(e.k), e.dist);
+    sig += buf;
+  }
+  uint64_t hsh = 1469598103934665603ull;  // FNV-1a
+  for (unsigned char c : sig) hsh = (hsh ^ c) * 1099511628211ull;
+  snprintf(buf, sizeof(buf), "%016llx", static_cast<unsigned long long>(hsh));
+  return std::string(buf);
+}
+
+int64_t cache_lookup(const std::string& sig) {
+  const char* path = getenv("SK_TUNE_CACHE");
+  if (!path) return 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return 0;
+  char line[256];
+  int64_t found = 0;
+  while (fgets(line, sizeof(line), f)) {
+    char s[64];
+    long long v;
+    if (sscanf(line, " \"%63[0-9a-f]\" : %lld", s, &v) == 2 && sig == s) found = v;
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const std::string& sig, int64_t value) {
+  const char* path = getenv("SK_TUNE_CACHE");
+  if (!path) return;
+  // keep the other entries: read, replace, rewrite as a flat JSON object
+  std::vector<std::pair<std::string, long long>> kv;
+  if (FILE* f = fopen(path, "r")) {
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+      char s[64];
+      long long v;
+      if (sscanf(line, " \"%63[0-9a-f]\" : %lld", s, &v) == 2 && sig != s) kv.emplace_back(s, v);
+    }
+    fclose(f);
+  }
+  kv.emplace_back(sig, static_cast<long long>(value));
+  if (FILE* f = fopen(path, "w")) {
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < kv.size(); ++i)
+      fprintf(f, "  \"%s\": %lld%s\n", kv[i].first.c_str(), kv[i].second,
+              i + 1 < kv.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+  }
+}
+
+void batch_invalidate(sk_batch* b) {
+  b->planned = false;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+sk_status to_status(cudaError_t e) { return sk::status_from_cuda(e); }
+
+// Plan every member with items of about `item_stages` stages of 16 rows.
+sk_status batch_plan(sk_batch* b, int64_t item_stages, cudaStream_t st) {
+  using namespace sk;
+  std::vector<LeftPlan> plans;
+  std::vector<GemmShape> shapes;
+  size_t part_total = 0;
+  std::vector<size_t> part_off;
+  for (const auto& e : b->entries) {
+    GemmShape s;
+    s.left = true;
+    s.P = e.k;
+    s.Q = e.n;
+    s.L = e.m;
+    LeftPlan pl = left_geometry(s, true);
+    const int64_t steps_total = (s.L + BK - 1) / BK;
+    set_splits(&pl, s, (steps_total + item_stages - 1) / item_stages);
+    // every member's partials start on a 256-byte boundary: the epilogue
+    // stores 16-byte vectors when n is a multiple of 4
+    part_off.push_back(part_total);
+    part_total += (static_cast<size_t>(pl.splits) * s.P * s.Q + 63) / 64 * 64;
+    plans.push_back(pl);
+    shapes.push_back(s);
+  }
+  cudaError_t ce = grow_device(&b->ws, &b->ws_bytes, part_total * sizeof(float) + 256);
+  if (ce != cudaSuccess) return to_status(ce);
+  b->hs = HostSched();
+  b->hs.probs.resize(plans.size());
+  for (size_t i = 0; i < plans.size(); ++i) {
+    const auto& e = b->entries[i];
+    if (!fill_problem(&b->hs.probs[i], plans[i], shapes[i], e.A, e.lda,
+                      static_cast<float*>(b->ws) + part_off[i], e.seed, e.dist))
+      return SK_EINVAL;
+  }
+  const int64_t slots = pair_slots();
+  if (slots <= 0) return SK_EUNSUPPORTED;
+  build_items(plans, slots / 2, &b->hs);
+  pack_sched(&b->hs);
+  b->units = static_cast<int64_t>(b->hs.begin.size()) - 1;
+  b->red.clear();
+  b->max_elems = 0;
+  for (size_t i = 0; i < plans.size(); ++i) {
+    const auto& e = b->entries[i];
+    ReduceDesc d;
+    d.part = static_cast<float*>(b->ws) + part_off[i];
+    d.Y = e.Y;
+    d.P = e.k;
+    d.Q = e.n;
+    d.ldy = e.ldy;
+    d.splits = plans[i].splits;
+    d.scale = e.scale;
+    b->red.push_back(d);
+    b->max_elems = std::max<int64_t>(b->max_elems, e.k * e.n);
+  }
+  b->off_red = (b->hs.bytes + 255) / 256 * 256;
+  const size_t total = b->off_red + b->red.size() * sizeof(ReduceDesc);
+  ce = grow_device(&b->d_buf, &b->d_bytes, total);
+  if (ce != cudaSuccess) return to_status(ce);
+  ce = cudaMemcpyAsync(b->d_buf, b->hs.blob.data(), b->hs.bytes, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(static_cast<uint8_t*>(b->d_buf) + b->off_red, b->red.data(),
+                         b->red.size() * sizeof(ReduceDesc), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host images may change later
+  if (ce != cudaSuccess) return to_status(ce);
+  b->planned = true;
+  return SK_OK;
+}
+
+// The two launches of a batch run.
+cudaError_t batch_launch(sk_batch* b, cudaStream_t st) {
+  using namespace sk;
+  const LeftSched sc = device_sched(b->hs, b->d_buf, b->d_status);
+  cudaError_t e = launch_left<true>(sc, b->units, st);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  return splitk_reduce_batched(
+      reinterpret_cast<const ReduceDesc*>(static_cast<uint8_t*>(b->d_buf) + b->off_red),
+      static_cast<int>(b->red.size()), b->max_elems, st);
+}
+
+sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
+  // the legacy default stream cannot be captured: launch directly there
+  if (!use_graph || st == nullptr) return to_status(batch_launch(b, st));
+  if (b->graph == nullptr) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return to_status(e);
+    const cudaError_t le = batch_launch(b, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return to_status(le != cudaSuccess ? le : e);
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return to_status(e);
+    }
+  }
+  return to_status(cudaGraphLaunch(b->graph, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+sk_status sk_batch_create(sk_batch_handle* out) {
+  if (!out) return SK_EINVAL;
+  *out = nullptr;
+  sk_batch* b = new (std::nothrow) sk_batch;
+  if (!b) return SK_ENOMEM;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    if (b->d_status) cudaFree(b->d_status);
+    delete b;
+    return to_status(e);
+  }
+  *out = b;
+  return SK_OK;
+}
+
+sk_status sk_batch_add(sk_batch_handle b, sk_handle h, const float* A, int64_t m, int64_t n,
+                       int64_t lda, float* Y, int64_t ldy) {
+  if (!b || !h || !A || !Y || m <= 0 || n <= 0 || lda < n || ldy < n) return SK_EINVAL;
+  if (m >= (1LL << 31) - 64) return SK_EINVAL;
+  if (h->prec != SK_BF16X2) return SK_EUNSUPPORTED;
+  sk::GemmShape s;
+  s.left = true;
+  s.P = h->k;
+  s.Q = n;
+  s.L = m;
+  const sk_status st = sk::tc_check(s, A, lda, Y, ldy);
+  if (st != SK_OK) return st;
+  sk_batch::Entry e{h->seed, h->dist, h->k, h->scale, A, m, n, lda, Y, ldy};
+  b->entries.push_back(e);
+  batch_invalidate(b);
+  return SK_OK;
+}
+
+sk_status sk_batch_run(sk_batch_handle b, void* stream) {
+  if (!b || b->entries.empty()) return SK_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!b->planned) {
+    int64_t t = b->item_stages;
+    if (t <= 0) t = cache_lookup(batch_signature(b));
+    if (t <= 0) t = kDefaultItemStages;
+    const sk_status ps = batch_plan(b, t, st);
+    if (ps != SK_OK) return ps;
+  }
+  return batch_run_once(b, st, true);
+}
+
+sk_status sk_batch_tune(sk_batch_handle b, void* stream, int64_t* chosen) {
+  if (!b || b->entries.empty()) return SK_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t cands[] = {128, 256, 512, 1024, 2048, 4096};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return to_status(cudaGetLastError());
+  float best_ms = 1e30f;
+  int64_t best = kDefaultItemStages;
+  sk_status rs = SK_OK;
+  for (int64_t t : cands) {
+    batch_invalidate(b);
+    rs = batch_plan(b, t, st);
+    if (rs != SK_OK) break;
+    rs = batch_run_once(b, st, false);  // warm-up
+    if (rs != SK_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rs == SK_OK; ++r) rs = batch_run_once(b, st, false);
+    cudaEventRecord(e1, st);
+    if (rs != SK_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_invalidate(b);
+  if (rs != SK_OK) return rs;
+  b->item_stages = best;
+  cache_store(batch_signature(b), best);
+  if (chosen) *chosen = best;
+  return SK_OK;
+}
+
+sk_status sk_batch_status(sk_batch_handle b, void* stream) {
+  if (!b) return SK_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  int word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(b->d_status, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) return to_status(e);
+  return static_cast<sk_status>(word);
+}
+
+sk_status sk_batch_size(sk_batch_handle b, int64_t* count) {
+  if (!b || !count) return SK_EINVAL;
+  *count = static_cast<int64_t>(b->entries.size());
+  return SK_OK;
+}
+
+sk_status sk_batch_destroy(sk_batch_handle b) {
+  if (!b) return SK_EINVAL;
+  batch_invalidate(b);
+  if (b->d_buf) cudaFree(b->d_buf);
+  if (b->ws) cudaFree(b->ws);
+  if (b->d_status) cudaFree(b->d_status);
+  delete b;
+  return SK_OK;
+}
+
+}  // extern "C"
