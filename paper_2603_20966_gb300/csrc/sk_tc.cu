@@ -279,8 +279,11 @@ __device__ __forceinline__ void convert_stage(const float* stg, uint8_t* bhi, ui
 
 // Persistent left-sketch kernel: each pair (or single CTA) runs its list of
 // items back to back; ring positions, barrier phases and accumulation chains
-// are counted across items (g = stage counter, gc = chain counter).
-template <bool PAIR>
+// are counted across items (g = stage counter, gc = chain counter).  DIST is
+// the distribution of every item, or kMixed to read it per item (batches).
+constexpr int kMixed = -1;
+
+template <int DIST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_sketch_bf16x2_left(const LeftSched sc) {
   using C = Cfg<PAIR>;
@@ -521,7 +524,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
         const int64_t cbase = ig.lbeg + static_cast<int64_t>(s) * BK;
-        if (ig.dist == kRademacher)
+        if (DIST != kMixed)
+          gen_stage<DIST, C>(sdst, ig, cbase, wt, cached_blk, words);
+        else if (ig.dist == kRademacher)
           gen_stage<kRademacher, C>(sdst, ig, cbase, wt, cached_blk, words);
         else if (ig.dist == kUniform)
           gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
@@ -897,11 +902,11 @@ int num_sms_tc() {
   return sms;
 }
 
-template <bool PAIR>
+template <int DIST, bool PAIR>
 cudaError_t set_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<PAIR>,
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
   if (e == cudaSuccess) done = true;
   return e;
@@ -927,12 +932,12 @@ void fill_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, dim3 grid, 
 int64_t pair_slots() {
   static int64_t cache = 0;
   if (cache != 0) return cache;
-  if (set_smem_attr<true>() != cudaSuccess) return cache = -1;
+  if (set_smem_attr<kMixed, true>() != cudaSuccess) return cache = -1;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   fill_config<true>(&cfg, attr, dim3(2, 1, 1), nullptr);
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_left<true>, &cfg) !=
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_left<kMixed, true>, &cfg) !=
           cudaSuccess ||
       clusters <= 0) {
     cudaGetLastError();
@@ -1101,14 +1106,21 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
   return sc;
 }
 
-template <bool PAIR>
+template <int DIST, bool PAIR>
 cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
-  cudaError_t e = set_smem_attr<PAIR>();
+  cudaError_t e = set_smem_attr<DIST, PAIR>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   fill_config<PAIR>(&cfg, attr, dim3(static_cast<unsigned>(units * (PAIR ? 2 : 1)), 1, 1), st);
-  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<PAIR>, sc);
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR>, sc);
+}
+
+template <bool PAIR>
+cudaError_t launch_left_dist(int dist, const LeftSched& sc, int64_t units, cudaStream_t st) {
+  if (dist == kRademacher) return launch_left<kRademacher, PAIR>(sc, units, st);
+  if (dist == kUniform) return launch_left<kUniform, PAIR>(sc, units, st);
+  return launch_left<kGaussian, PAIR>(sc, units, st);
 }
 
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const float* A,
@@ -1293,8 +1305,8 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status);
   const int64_t nunits = static_cast<int64_t>(hs.begin.size()) - 1;
   prof_mark(h->prof_start, st);
-  const cudaError_t e = pl.pair ? launch_left<true>(sc, nunits, st)
-                                : launch_left<false>(sc, nunits, st);
+  const cudaError_t e = pl.pair ? launch_left_dist<true>(h->dist, sc, nunits, st)
+                                : launch_left_dist<false>(h->dist, sc, nunits, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
@@ -1473,13 +1485,12 @@ sk_status batch_plan(sk_batch* b, int64_t item_stages, cudaStream_t st) {
   return SK_OK;
 }
 
-// The two launches of a batch run.
+// The two launches of a batch run (counted by the caller).
 cudaError_t batch_launch(sk_batch* b, cudaStream_t st) {
   using namespace sk;
   const LeftSched sc = device_sched(b->hs, b->d_buf, b->d_status);
-  cudaError_t e = launch_left<true>(sc, b->units, st);
+  cudaError_t e = launch_left<kMixed, true>(sc, b->units, st);
   if (e != cudaSuccess) return e;
-  count_launches(1);
   return splitk_reduce_batched(
       reinterpret_cast<const ReduceDesc*>(static_cast<uint8_t*>(b->d_buf) + b->off_red),
       static_cast<int>(b->red.size()), b->max_elems, st);
@@ -1487,7 +1498,11 @@ cudaError_t batch_launch(sk_batch* b, cudaStream_t st) {
 
 sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
   // the legacy default stream cannot be captured: launch directly there
-  if (!use_graph || st == nullptr) return to_status(batch_launch(b, st));
+  if (!use_graph || st == nullptr) {
+    const cudaError_t e = batch_launch(b, st);
+    if (e == cudaSuccess) sk::count_launches(1);  // the reduce counted itself
+    return to_status(e);
+  }
   if (b->graph == nullptr) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -1505,7 +1520,9 @@ sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
       return to_status(e);
     }
   }
-  return to_status(cudaGraphLaunch(b->graph, st));
+  const cudaError_t e = cudaGraphLaunch(b->graph, st);
+  if (e == cudaSuccess) sk::count_launches(2);  // the sketch and the reduce kernels
+  return to_status(e);
 }
 
 }  // namespace
