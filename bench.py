@@ -5,7 +5,10 @@ One step = the left sketches Y = S A of the tall-skinny workload
 Gaussian S, both regenerated inside the kernels from Philox4x32-10.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x2|fp32]
-                  [--impl ours|reference] [--workload C2|C1]
+                  [--impl ours|reference] [--workload C1|C2|C3|C4|C5]
+
+C1-C3 time single sketches, C4 a batch of 256 sketches in one persistent
+launch, C5 the request server under a Poisson stream (latency percentiles).
 
 Prints ONE JSON line (rank 0).  `value` is useful TFLOP/s (2 k m n per
 sketch) over the whole job; `roofline` describes the dominant kernel (the
@@ -37,6 +40,7 @@ WORKLOADS = {
     "C1": (4096, 256, 64, (0,), "left"),
     "C3": (65536, 16384, 256, (0,), "right"),
     "C4": (None, None, None, (0, 1), "batch"),
+    "C5": (None, None, None, (0, 1), "serve"),
 }
 DIST_NAME = {0: "gaussian", 1: "rademacher", 2: "uniform"}
 METRIC = "fused gen+sketch TFLOP/s and % roofline vs plain FP32; served p50/p99 latency"
@@ -296,6 +300,176 @@ def run_batch(args):
     return 0
 
 
+def _serve_stream(P, srv, reqs, hs, src_ptr, src_ld, fetch=None):
+    """Submit `reqs` at their arrival times (busy-waiting on the host clock)
+    and wait until every one has finished.  Returns (wall seconds from the
+    first submission to the last completion, max submission lateness s)."""
+    import torch
+    tickets = []
+    late = 0.0
+    done = threading.Event()
+    errors = []
+
+    def collect():
+        # fetch results in submission order (e2e leg): Y to pinned host memory
+        i = 0
+        while i < len(reqs):
+            if i >= len(tickets):
+                time.sleep(0.0002)
+                continue
+            r, t = reqs[i], tickets[i]
+            st, _ = P.sk_server_wait(srv, t, 120.0)
+            if st != 0:
+                errors.append(P.status_string(st))
+                break
+            P.sk_server_fetch(srv, t, fetch, r.prob.n)
+            i += 1
+        done.set()
+
+    th = None
+    if fetch is not None:
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        target = t0 + r.arrival_s
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 0.002:
+                time.sleep(0.001)
+        late = max(late, time.perf_counter() - target)
+        p = r.prob
+        t = P.sk_server_submit(srv, hs[i], src_ptr + 4 * r.row0 * src_ld, p.m, p.n, src_ld)
+        if fetch is None:
+            P.sk_server_release(srv, t)  # results dropped when they finish
+        tickets.append(t)
+    deadline = time.perf_counter() + 180.0
+    if th is not None:
+        done.wait(timeout=180.0)
+        if errors or not done.is_set():
+            raise RuntimeError(f"serving e2e leg failed: {errors or 'timeout'}")
+    else:
+        while time.perf_counter() < deadline:
+            s = P.sk_server_stats_get(srv)
+            if s["completed"] + s["failed"] >= len(reqs):
+                break
+            time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    s = P.sk_server_stats_get(srv)
+    if s["failed"] or s["completed"] < len(reqs):
+        raise RuntimeError(f"serving run incomplete: {s}")
+    return wall, late
+
+
+def run_serve(args):
+    """C5: a Poisson stream of left-sketch requests (2000/s, m log-uniform in
+    [1024, 2^18], n uniform in [32, 512], k = 2n) through the request server
+    with a 120 GB budget; BF16 split-A and plain FP32 forms; p50/p99 latency
+    (arrival to Y ready) and served useful TFLOP/s."""
+    import torch
+
+    import paper_2603_20966_gb300 as P
+    from paper_2603_20966_gb300.workloads import gaussian_matrix, serving_requests
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+    count = args.serve_requests
+    reqs = serving_requests(count, seed=3000 + 1000 * rank)
+    src_rows, src_ld = 1 << 18, 512
+    # the load generator's source rows: every request reads a window of them
+    src = gaussian_matrix(src_rows, src_ld, 77 + rank, device=dev)
+    src_host = torch.empty((src_rows, src_ld), dtype=torch.float32, pin_memory=True)
+    src_host.copy_(src)
+    torch.cuda.synchronize(dev)
+    budget = 120 * 10**9
+    forms = [("bf16x2", P.SK_BF16X2), ("fp32", P.SK_FP32)]
+    out = {}
+    launches = 0
+    clocks = ClockSampler(local)
+    clk = None
+    e2e = None
+    for name, form in forms:
+        hs = []
+        for r in reqs:
+            h = P.sk_create(r.prob.seed, r.prob.dist, r.prob.k)
+            if form != P.SK_FP32:
+                P.sk_set_precision(h, form)
+            hs.append(h)
+        srv = P.sk_server_create(budget, 4096)
+        try:
+            # warm-up: one request of each distinct small shape class
+            warm = reqs[:max(3, args.warmup) * 10]
+            _serve_stream(P, srv, [type(r)(0.0, r.prob, r.row0) for r in warm], hs,
+                          src.data_ptr(), src_ld)
+            P.sk_server_reset_stats(srv)
+            if world > 1:
+                tdist.barrier()
+            if name == "bf16x2":
+                clocks.start()
+            l0 = P.sk_launch_count()
+            wall, late = _serve_stream(P, srv, reqs, hs, src.data_ptr(), src_ld)
+            launches += P.sk_launch_count() - l0
+            if name == "bf16x2":
+                clk = clocks.stop()
+            st = P.sk_server_stats_get(srv)
+            out[name] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                         "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+                         "mean_wait_ms": st["mean_wait_ms"],
+                         "served_tflops": st["flops"] / wall / 1e12,
+                         "wall_s": wall, "steps": st["steps"],
+                         "mean_requests_per_step": count / max(1, st["steps"]),
+                         "max_step_requests": st["max_step_requests"],
+                         "peak_pool_gb": st["peak_bytes"] / 1e9,
+                         "max_submit_lateness_ms": late * 1e3}
+            if name == "bf16x2" and not args.no_e2e:
+                # end to end: sources in pinned host memory (copied in at
+                # admission), every Y fetched back to pinned host memory
+                P.sk_server_reset_stats(srv)
+                y_host = torch.empty((1024, 512), dtype=torch.float32, pin_memory=True)
+                wall_e, _ = _serve_stream(P, srv, reqs, hs, src_host.data_ptr(), src_ld,
+                                          fetch=y_host)
+                st = P.sk_server_stats_get(srv)
+                e2e = {"value": st["flops"] / wall_e / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": sum(4 * r.prob.m * r.prob.n for r in reqs),
+                       "d2h_bytes_per_step": sum(4 * r.prob.k * r.prob.n for r in reqs),
+                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "wall_s": wall_e,
+                       "step": f"the whole {count}-request stream from pinned host sources, "
+                               "results fetched to pinned host memory"}
+        finally:
+            P.sk_server_destroy(srv)
+            for h in hs:
+                P.sk_destroy(h)
+    flops = sum(2.0 * r.prob.k * r.prob.m * r.prob.n for r in reqs)
+    offered = flops / reqs[-1].arrival_s / 1e12
+    if rank == 0:
+        b = out["bf16x2"]
+        line = {
+            "metric": METRIC, "value": b["served_tflops"] * world, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": count, "warmup": args.warmup,
+            "ms_per_step": b["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x2", "data": "synthetic",
+            "config": {"workload": f"C5 serving: Poisson stream of {count} left-sketch "
+                                   "requests at 2000/s, m log-uniform [1024, 2^18], n uniform "
+                                   "[32, 512], k = 2n, mixed Gaussian/Rademacher, 120 GB budget",
+                       "offered_tflops": offered, "useful_tflop": flops / 1e12,
+                       "step": "one step = one request; ms_per_step = mean latency",
+                       "l2": "request windows drawn from a 512 MiB source, larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"bf16x2": {"p50": b["p50_ms"], "p99": b["p99_ms"]},
+                           "fp32": {"p50": out["fp32"]["p50_ms"], "p99": out["fp32"]["p99_ms"]}},
+            "forms": out, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -484,6 +658,7 @@ def main():
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -491,6 +666,8 @@ def main():
         return run_reference(args)
     if WORKLOADS[args.workload][4] == "batch":
         return run_batch(args)
+    if WORKLOADS[args.workload][4] == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -223,6 +223,108 @@ sk_status sk_batch_size(sk_batch_handle b, int64_t* count);
 /* Release the batch and its device buffers (not the members' handles). */
 sk_status sk_batch_destroy(sk_batch_handle b);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of left sketches under an HBM budget.
+ *
+ * The paper sketches one matrix per call (Sec. 3 problem statement); a
+ * server turns the same operation into a request stream.  A server owns one
+ * device pool of `hbm_budget_bytes` (allocated at creation) and a host
+ * scheduler thread.  sk_server_submit enqueues a request for the left sketch
+ * Y[k x n] = S[k x m] A[m x n] of a handle; the request's arrival time is the
+ * time of the call.  The scheduler:
+ *  - admits pending requests strictly in arrival order while the next one
+ *    fits in the pool and fewer than `max_slots` requests are resident; an
+ *    admitted request receives pool memory for a copy of A (row stride n
+ *    rounded up to 4), for Y (same stride) and for its split partials, and
+ *    A is copied in on a copy stream;
+ *  - at each step boundary (one of its two compute streams idle) launches
+ *    every admitted request not yet launched as one step: the SK_BF16X2
+ *    requests as one persistent batched launch plus one batched reduce
+ *    (as sk_batch_run), the SK_FP32 requests as fused SIMT launches.  Steps
+ *    on the two streams overlap on the device, so requests arriving while
+ *    others run join the next step without waiting for the GPU to drain;
+ *  - completes a step when its event is observed; the copy of A and the
+ *    partials go back to the pool, Y stays there until fetched or released.
+ * Latency = arrival to the observation of the completion (host steady
+ * clock).  Work items have a fixed length (512 stages of 16 rows), so a
+ * request's decomposition, its accumulation order and its result depend
+ * only on its own (seed, dist, k, precision, A), never on the mix.
+ * All server calls are thread-safe. */
+typedef struct sk_server* sk_server_handle;
+
+typedef struct {
+  int64_t submitted;          /* requests accepted by sk_server_submit */
+  int64_t completed;          /* finished without error */
+  int64_t failed;             /* finished with a device error */
+  int64_t pending;            /* waiting for admission */
+  int64_t resident;           /* holding pool memory (admitted, running or done) */
+  int64_t steps;              /* steps launched */
+  int64_t max_step_requests;  /* most requests in one step */
+  double p50_ms, p99_ms;      /* latency percentiles of completed requests */
+  double mean_ms, max_ms;
+  double mean_wait_ms;        /* arrival to launch, mean over completed */
+  double flops;               /* 2 k m n summed over completed requests */
+  double busy_s;              /* first arrival to last completion, seconds */
+  uint64_t pool_bytes;        /* size of the pool */
+  uint64_t peak_bytes;        /* most pool bytes in use at once */
+} sk_server_stats;
+
+/* Create a server on the current device with a pool of `hbm_budget_bytes`
+ * (rounded up to 256) and at most `max_slots` resident requests (>= 1).
+ * Errors: SK_EINVAL, SK_ENOMEM (pool allocation), SK_ECUDA. */
+sk_status sk_server_create(uint64_t hbm_budget_bytes, int32_t max_slots,
+                           sk_server_handle* out);
+
+/* Submit Y = S A for handle `h` (form SK_BF16X2 or SK_FP32; seed, dist, k and
+ * form are read now, the handle may be destroyed afterwards).  A[m x n] with
+ * leading dimension lda is a host or device pointer (unified addressing).
+ * The server records an event on `stream` (the stream that produces A; NULL
+ * = the legacy default stream) and copies A only after it, so A may still be
+ * in production on that stream; A must stay valid and unchanged until the
+ * request completes or fails.  Device memory, managed memory and mapped
+ * pinned host memory are read by a copy kernel, pageable host memory through
+ * the copy engine.  On success *ticket identifies the request.  Errors:
+ * SK_EINVAL, SK_EUNSUPPORTED (other forms), SK_EBUDGET (the request alone
+ * needs more than the whole pool; nothing is enqueued), SK_ECANCELLED
+ * (server shutting down), SK_ECUDA. */
+sk_status sk_server_submit(sk_server_handle s, sk_handle h, const float* A, int64_t m,
+                           int64_t n, int64_t lda, void* stream, int64_t* ticket);
+
+/* Non-blocking: SK_OK when the request has completed (then *latency_ms, if
+ * not NULL, receives its latency), SK_EBUSY while pending or running, the
+ * device error (e.g. SK_ETIMEOUT) if it failed, SK_EINVAL for an unknown or
+ * released ticket. */
+sk_status sk_server_poll(sk_server_handle s, int64_t ticket, double* latency_ms);
+
+/* As sk_server_poll, but blocks up to `timeout_s` seconds for completion;
+ * SK_EBUSY when the time ran out. */
+sk_status sk_server_wait(sk_server_handle s, int64_t ticket, double timeout_s,
+                         double* latency_ms);
+
+/* Copy the completed request's Y[k x n] into `Y` (host or device pointer,
+ * leading dimension ldy >= n) on `stream`, after the work already enqueued
+ * there, wait for the copy and release the request.  Errors: SK_EBUSY (not
+ * complete), the request's device error (the request is released),
+ * SK_EINVAL, SK_ECUDA (the result is kept; the call may be repeated). */
+sk_status sk_server_fetch(sk_server_handle s, int64_t ticket, float* Y, int64_t ldy,
+                          void* stream);
+
+/* Release a request: its pool memory is returned now if it has finished,
+ * else as soon as it finishes (its latency still counts).  SK_EINVAL for an
+ * unknown ticket. */
+sk_status sk_server_release(sk_server_handle s, int64_t ticket);
+
+/* Snapshot of the server's counters and latency percentiles. */
+sk_status sk_server_stats_get(sk_server_handle s, sk_server_stats* out);
+
+/* Clear the latency samples and counters of finished requests (pending and
+ * resident requests are kept). */
+sk_status sk_server_reset_stats(sk_server_handle s);
+
+/* Stop admitting, wait for launched steps to finish (pending requests are
+ * cancelled), release the pool and the server. */
+sk_status sk_server_destroy(sk_server_handle s);
+
 /* Synchronise `stream` and copy the handle's four device status words
  * without clearing them: [0] the sk_status sk_stream_status would return,
  * [1] where the first bounded wait that gave up was waiting (role * 16 +

@@ -15,7 +15,10 @@ from ._native import (SK_BF16X2, sk_batch_add, sk_batch_create, sk_batch_destroy
                       sk_profile_events,
                       sk_set_precision, sk_set_workspace, sk_stream_status, sk_version,
                       sk_workspace_size, status_string)
-from .sketch import Sketch
+from ._native import (sk_server_create, sk_server_destroy, sk_server_fetch, sk_server_poll,
+                      sk_server_release, sk_server_reset_stats, sk_server_stats_get,
+                      sk_server_submit, sk_server_wait)
+from .sketch import Server, Sketch
 
 __all__ = [
     "Sketch", "SketchError", "SK_GAUSSIAN", "SK_RADEMACHER", "SK_UNIFORM", "SK_FP32", "SK_BF16X2",
@@ -23,5 +26,7 @@ __all__ = [
     "sk_apply_right", "sk_apply_left_host", "sk_apply_right_host", "sk_materialize",
     "sk_workspace_size", "sk_set_workspace", "sk_stream_status", "sk_debug_status", "sk_destroy", "sk_version", "sk_profile_events", "sk_launch_count",
     "status_string", "sk_batch_create", "sk_batch_add", "sk_batch_run", "sk_batch_tune",
-    "sk_batch_status", "sk_batch_size", "sk_batch_destroy",
+    "sk_batch_status", "sk_batch_size", "sk_batch_destroy", "Server", "sk_server_create",
+    "sk_server_submit", "sk_server_poll", "sk_server_wait", "sk_server_fetch",
+    "sk_server_release", "sk_server_stats_get", "sk_server_reset_stats", "sk_server_destroy",
 ]

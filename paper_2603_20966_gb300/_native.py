@@ -45,6 +45,15 @@ PROTOTYPES = {
     "sk_batch_status": (_int, [_vp, _vp]),
     "sk_batch_size": (_int, [_vp, _P(_i64)]),
     "sk_batch_destroy": (_int, [_vp]),
+    "sk_server_create": (_int, [_u64, ctypes.c_int32, _P(_vp)]),
+    "sk_server_submit": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _P(_i64)]),
+    "sk_server_poll": (_int, [_vp, _i64, _P(ctypes.c_double)]),
+    "sk_server_wait": (_int, [_vp, _i64, ctypes.c_double, _P(ctypes.c_double)]),
+    "sk_server_fetch": (_int, [_vp, _i64, _vp, _i64, _vp]),
+    "sk_server_release": (_int, [_vp, _i64]),
+    "sk_server_stats_get": (_int, [_vp, _vp]),
+    "sk_server_reset_stats": (_int, [_vp]),
+    "sk_server_destroy": (_int, [_vp]),
     "sk_destroy": (_int, [_vp]),
     "sk_profile_events": (_int, [_vp, _vp, _vp]),
     "sk_launch_count": (ctypes.c_uint64, []),
@@ -256,3 +265,67 @@ def sk_batch_destroy(b) -> None:
 
 def sk_destroy(h) -> None:
     _check("sk_destroy", _lib.sk_destroy(h))
+
+
+class ServerStats(ctypes.Structure):
+    """Mirror of ``sk_server_stats``."""
+    _fields_ = [
+        ("submitted", _i64), ("completed", _i64), ("failed", _i64), ("pending", _i64),
+        ("resident", _i64), ("steps", _i64), ("max_step_requests", _i64),
+        ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double), ("mean_wait_ms", ctypes.c_double),
+        ("flops", ctypes.c_double), ("busy_s", ctypes.c_double),
+        ("pool_bytes", _u64), ("peak_bytes", _u64),
+    ]
+
+
+def sk_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
+    s = ctypes.c_void_p()
+    _check("sk_server_create", _lib.sk_server_create(int(hbm_budget_bytes), int(max_slots),
+                                                     ctypes.byref(s)))
+    return s.value
+
+
+def sk_server_submit(s, h, A, m, n, lda, stream=None) -> int:
+    """`stream`: the stream producing A (the copy of A waits for it)."""
+    t = ctypes.c_int64()
+    _check("sk_server_submit", _lib.sk_server_submit(s, h, _ptr(A), int(m), int(n), int(lda),
+                                                     _stream(stream), ctypes.byref(t)))
+    return t.value
+
+
+def sk_server_poll(s, ticket) -> tuple[int, float]:
+    """(status, latency_ms): SK_OK when done, SK_EBUSY while pending or running."""
+    lat = ctypes.c_double(0.0)
+    st = _lib.sk_server_poll(s, int(ticket), ctypes.byref(lat))
+    return st, lat.value
+
+
+def sk_server_wait(s, ticket, timeout_s: float) -> tuple[int, float]:
+    lat = ctypes.c_double(0.0)
+    st = _lib.sk_server_wait(s, int(ticket), float(timeout_s), ctypes.byref(lat))
+    return st, lat.value
+
+
+def sk_server_fetch(s, ticket, Y, ldy, stream=None) -> None:
+    """Copy Y out on `stream` (after the work queued there) and release it."""
+    _check("sk_server_fetch", _lib.sk_server_fetch(s, int(ticket), _ptr(Y), int(ldy),
+                                                   _stream(stream)))
+
+
+def sk_server_release(s, ticket) -> None:
+    _check("sk_server_release", _lib.sk_server_release(s, int(ticket)))
+
+
+def sk_server_stats_get(s) -> dict:
+    out = ServerStats()
+    _check("sk_server_stats_get", _lib.sk_server_stats_get(s, ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in ServerStats._fields_}
+
+
+def sk_server_reset_stats(s) -> None:
+    _check("sk_server_reset_stats", _lib.sk_server_reset_stats(s))
+
+
+def sk_server_destroy(s) -> None:
+    _check("sk_server_destroy", _lib.sk_server_destroy(s))

@@ -71,6 +71,45 @@ struct ReduceDesc {
 cudaError_t splitk_reduce_batched(const ReduceDesc* d_desc, int nprob, int64_t max_elems,
                                   cudaStream_t st);
 
+// ---- batches of left sketches on the tensor cores (sk_tc.cu) ----
+struct BatchMember {
+  uint64_t seed;
+  int dist;
+  int64_t k;
+  float scale;
+  const float* A;
+  int64_t m, n, lda;
+  float* Y;
+  int64_t ldy;
+  float* part = nullptr;  // own split partials (batch_member_workspace bytes), or null
+  int64_t item_stages = 0;  // own work-item length in stages of 16 rows, or 0
+};
+// Device buffers one batch launch uses; grown on demand, owned by the caller.
+struct BatchArena {
+  void* d_buf = nullptr;  // work list + reduce descriptors
+  size_t d_bytes = 0;
+  void* ws = nullptr;     // split partials of the members without their own
+  size_t ws_bytes = 0;
+  int* d_status = nullptr;
+  // pinned staging of the work list: when set, uploads do not synchronise
+  // (the caller guarantees the previous launch from this arena has finished)
+  bool async_upload = false;
+  void* h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+};
+// Work-item length (stages of 16 rows) that spreads one left sketch over all
+// CTA pairs of the GPU when it runs alone (items of at least 64 stages); a
+// function of the shape only.
+int64_t spread_item_stages(const BatchMember& mb);
+// Bytes of partials a member needs with items of `item_stages` stages.
+size_t batch_member_workspace(const BatchMember& mb, int64_t item_stages);
+// Plan the members (items of about `item_stages` stages), upload the work
+// list into `arena` on `st` (synchronising `st`), make `st` wait for
+// `ready` (may be null) and launch the persistent sketch kernel and the
+// batched reduction on `st`.
+cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t item_stages,
+                                 BatchArena* arena, cudaEvent_t ready, cudaStream_t st);
+
 // ---- BF16 split-A tensor-core form (sk_tc.cu) ----
 size_t tc_workspace_bytes(const GemmShape& s);
 sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float* Y, int64_t ldy);

@@ -1314,39 +1314,178 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   return splitk_reduce(static_cast<float*>(ws), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
 }
 
+struct PlannedBatch {
+  HostSched hs;
+  std::vector<ReduceDesc> red;
+  size_t off_red = 0;
+  size_t ws_floats = 0;
+  int64_t max_elems = 0;
+  int64_t units = 0;
+};
+
+LeftPlan member_plan(const BatchMember& mb, int64_t item_stages, GemmShape* shape) {
+  if (mb.item_stages > 0) item_stages = mb.item_stages;
+  GemmShape s;
+  s.left = true;
+  s.P = mb.k;
+  s.Q = mb.n;
+  s.L = mb.m;
+  LeftPlan pl = left_geometry(s, true);
+  const int64_t steps_total = (s.L + BK - 1) / BK;
+  set_splits(&pl, s, (steps_total + item_stages - 1) / item_stages);
+  if (shape) *shape = s;
+  return pl;
+}
+
+// Work list of a batch whose partials start at `ws`; with `ws` null only the
+// size of the partials (`ws_floats`) is computed.
+bool plan_members(const BatchMember* mbs, size_t count, int64_t item_stages, float* ws,
+                  PlannedBatch* pb) {
+  std::vector<LeftPlan> plans;
+  std::vector<GemmShape> shapes;
+  std::vector<size_t> part_off;
+  size_t total = 0;
+  for (size_t i = 0; i < count; ++i) {
+    GemmShape s;
+    plans.push_back(member_plan(mbs[i], item_stages, &s));
+    shapes.push_back(s);
+    // every member's partials start on a 256-byte boundary: the epilogue
+    // stores 16-byte vectors when n is a multiple of 4
+    part_off.push_back(total);
+    if (mbs[i].part == nullptr)
+      total += (static_cast<size_t>(plans.back().splits) * s.P * s.Q + 63) / 64 * 64;
+  }
+  pb->ws_floats = total;
+  if (ws == nullptr) return true;  // sizing pass
+  pb->hs = HostSched();
+  pb->hs.probs.resize(count);
+  for (size_t i = 0; i < count; ++i) {
+    float* part = mbs[i].part ? mbs[i].part : ws + part_off[i];
+    if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], mbs[i].A, mbs[i].lda, part,
+                      mbs[i].seed, mbs[i].dist))
+      return false;
+  }
+  const int64_t slots = pair_slots();
+  if (slots <= 0) return false;
+  build_items(plans, slots / 2, &pb->hs);
+  pack_sched(&pb->hs);
+  pb->units = static_cast<int64_t>(pb->hs.begin.size()) - 1;
+  pb->red.clear();
+  pb->max_elems = 0;
+  for (size_t i = 0; i < count; ++i) {
+    ReduceDesc d;
+    d.part = mbs[i].part ? mbs[i].part : ws + part_off[i];
+    d.Y = mbs[i].Y;
+    d.P = mbs[i].k;
+    d.Q = mbs[i].n;
+    d.ldy = mbs[i].ldy;
+    d.splits = plans[i].splits;
+    d.scale = mbs[i].scale;
+    pb->red.push_back(d);
+    pb->max_elems = std::max<int64_t>(pb->max_elems, mbs[i].k * mbs[i].n);
+  }
+  pb->off_red = (pb->hs.bytes + 255) / 256 * 256;
+  return true;
+}
+
+// Plan the members twice: once for the size of the partials, once with the
+// arena's workspace in place.
+cudaError_t plan_into_arena(const BatchMember* mbs, size_t count, int64_t item_stages,
+                            BatchArena* ar, PlannedBatch* pb) {
+  if (!plan_members(mbs, count, item_stages, nullptr, pb)) return cudaErrorInvalidValue;
+  const cudaError_t e = grow_device(&ar->ws, &ar->ws_bytes, pb->ws_floats * sizeof(float) + 256);
+  if (e != cudaSuccess) return e;
+  if (!plan_members(mbs, count, item_stages, static_cast<float*>(ar->ws), pb))
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+// Copy the work list and the reduce descriptors into the arena; waits for the
+// copies so that the host images may change afterwards.
+cudaError_t upload_plan(const PlannedBatch& pb, BatchArena* ar, cudaStream_t st) {
+  const size_t total = pb.off_red + pb.red.size() * sizeof(ReduceDesc);
+  cudaError_t e = grow_device(&ar->d_buf, &ar->d_bytes, total);
+  if (e != cudaSuccess) return e;
+  if (ar->async_upload) {
+    if (ar->h_stage_bytes < total) {
+      if (ar->h_stage) cudaFreeHost(ar->h_stage);
+      ar->h_stage = nullptr;
+      ar->h_stage_bytes = 0;
+      const size_t want = std::max<size_t>(total * 2, 1 << 16);
+      e = cudaHostAlloc(&ar->h_stage, want, cudaHostAllocDefault);
+      if (e != cudaSuccess) return e;
+      ar->h_stage_bytes = want;
+    }
+    uint8_t* h = static_cast<uint8_t*>(ar->h_stage);
+    memcpy(h, pb.hs.blob.data(), pb.hs.bytes);
+    memcpy(h + pb.off_red, pb.red.data(), pb.red.size() * sizeof(ReduceDesc));
+    return cudaMemcpyAsync(ar->d_buf, h, total, cudaMemcpyHostToDevice, st);
+  }
+  e = cudaMemcpyAsync(ar->d_buf, pb.hs.blob.data(), pb.hs.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<uint8_t*>(ar->d_buf) + pb.off_red, pb.red.data(),
+                        pb.red.size() * sizeof(ReduceDesc), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+// The persistent sketch launch and the batched reduce of an uploaded plan
+// (the caller counts them).
+cudaError_t launch_plan(const PlannedBatch& pb, const BatchArena& ar, cudaStream_t st) {
+  const LeftSched sc = device_sched(pb.hs, ar.d_buf, ar.d_status);
+  const cudaError_t e = launch_left<kMixed, true>(sc, pb.units, st);
+  if (e != cudaSuccess) return e;
+  return splitk_reduce_batched(
+      reinterpret_cast<const ReduceDesc*>(static_cast<uint8_t*>(ar.d_buf) + pb.off_red),
+      static_cast<int>(pb.red.size()), pb.max_elems, st);
+}
+
+int64_t spread_item_stages(const BatchMember& mb) {
+  GemmShape s;
+  s.left = true;
+  s.P = mb.k;
+  s.Q = mb.n;
+  s.L = mb.m;
+  const LeftPlan pl = left_geometry(s, true);
+  const int64_t units = std::max<int64_t>(1, pair_slots() / 2);
+  const int64_t tiles = pl.tiles_p * pl.tiles_q;
+  const int64_t steps_total = (s.L + BK - 1) / BK;
+  int64_t splits = (units + tiles - 1) / tiles;
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, steps_total / 64));
+  return (steps_total + splits - 1) / splits;
+}
+
+size_t batch_member_workspace(const BatchMember& mb, int64_t item_stages) {
+  GemmShape s;
+  const LeftPlan pl = member_plan(mb, item_stages, &s);
+  return ((static_cast<size_t>(pl.splits) * s.P * s.Q + 63) / 64 * 64) * sizeof(float);
+}
+
+cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t item_stages,
+                                 BatchArena* ar, cudaEvent_t ready, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  PlannedBatch pb;
+  cudaError_t e = plan_into_arena(mbs, count, item_stages, ar, &pb);
+  if (e == cudaSuccess) e = upload_plan(pb, ar, st);
+  if (e == cudaSuccess && ready) e = cudaStreamWaitEvent(st, ready, 0);
+  if (e == cudaSuccess) e = launch_plan(pb, *ar, st);
+  if (e == cudaSuccess) count_launches(1);  // the reduce counted itself
+  return e;
+}
+
 }  // namespace sk
 
 // ---------------------------------------------------------------------------
 // Batches (see include/sketch.h)
 // ---------------------------------------------------------------------------
 struct sk_batch {
-  struct Entry {
-    uint64_t seed;
-    int dist;
-    int64_t k;
-    float scale;
-    const float* A;
-    int64_t m, n, lda;
-    float* Y;
-    int64_t ldy;
-  };
-  std::vector<Entry> entries;
+  std::vector<sk::BatchMember> entries;
   int device = 0;
-  int* d_status = nullptr;
   int64_t item_stages = 0;  // tuned item length (stages); 0 = not chosen
   bool planned = false;
-  void* d_buf = nullptr;  // work list + reduce descriptors
-  size_t d_bytes = 0;
-  void* ws = nullptr;     // partials of every member
-  size_t ws_bytes = 0;
+  sk::BatchArena arena;     // work list, reduce descriptors, partials, status
+  sk::PlannedBatch plan;
   cudaGraphExec_t graph = nullptr;
-  cudaStream_t graph_stream = nullptr;
-  // plan results
-  sk::HostSched hs;
-  std::vector<sk::ReduceDesc> red;
-  size_t off_red = 0;
-  int64_t max_elems = 0;
-  int64_t units = 0;
 };
 
 namespace {
@@ -1420,80 +1559,17 @@ sk_status to_status(cudaError_t e) { return sk::status_from_cuda(e); }
 
 // Plan every member with items of about `item_stages` stages of 16 rows.
 sk_status batch_plan(sk_batch* b, int64_t item_stages, cudaStream_t st) {
-  using namespace sk;
-  std::vector<LeftPlan> plans;
-  std::vector<GemmShape> shapes;
-  size_t part_total = 0;
-  std::vector<size_t> part_off;
-  for (const auto& e : b->entries) {
-    GemmShape s;
-    s.left = true;
-    s.P = e.k;
-    s.Q = e.n;
-    s.L = e.m;
-    LeftPlan pl = left_geometry(s, true);
-    const int64_t steps_total = (s.L + BK - 1) / BK;
-    set_splits(&pl, s, (steps_total + item_stages - 1) / item_stages);
-    // every member's partials start on a 256-byte boundary: the epilogue
-    // stores 16-byte vectors when n is a multiple of 4
-    part_off.push_back(part_total);
-    part_total += (static_cast<size_t>(pl.splits) * s.P * s.Q + 63) / 64 * 64;
-    plans.push_back(pl);
-    shapes.push_back(s);
-  }
-  cudaError_t ce = grow_device(&b->ws, &b->ws_bytes, part_total * sizeof(float) + 256);
-  if (ce != cudaSuccess) return to_status(ce);
-  b->hs = HostSched();
-  b->hs.probs.resize(plans.size());
-  for (size_t i = 0; i < plans.size(); ++i) {
-    const auto& e = b->entries[i];
-    if (!fill_problem(&b->hs.probs[i], plans[i], shapes[i], e.A, e.lda,
-                      static_cast<float*>(b->ws) + part_off[i], e.seed, e.dist))
-      return SK_EINVAL;
-  }
-  const int64_t slots = pair_slots();
-  if (slots <= 0) return SK_EUNSUPPORTED;
-  build_items(plans, slots / 2, &b->hs);
-  pack_sched(&b->hs);
-  b->units = static_cast<int64_t>(b->hs.begin.size()) - 1;
-  b->red.clear();
-  b->max_elems = 0;
-  for (size_t i = 0; i < plans.size(); ++i) {
-    const auto& e = b->entries[i];
-    ReduceDesc d;
-    d.part = static_cast<float*>(b->ws) + part_off[i];
-    d.Y = e.Y;
-    d.P = e.k;
-    d.Q = e.n;
-    d.ldy = e.ldy;
-    d.splits = plans[i].splits;
-    d.scale = e.scale;
-    b->red.push_back(d);
-    b->max_elems = std::max<int64_t>(b->max_elems, e.k * e.n);
-  }
-  b->off_red = (b->hs.bytes + 255) / 256 * 256;
-  const size_t total = b->off_red + b->red.size() * sizeof(ReduceDesc);
-  ce = grow_device(&b->d_buf, &b->d_bytes, total);
-  if (ce != cudaSuccess) return to_status(ce);
-  ce = cudaMemcpyAsync(b->d_buf, b->hs.blob.data(), b->hs.bytes, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(static_cast<uint8_t*>(b->d_buf) + b->off_red, b->red.data(),
-                         b->red.size() * sizeof(ReduceDesc), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host images may change later
-  if (ce != cudaSuccess) return to_status(ce);
+  cudaError_t e = sk::plan_into_arena(b->entries.data(), b->entries.size(), item_stages,
+                                      &b->arena, &b->plan);
+  if (e == cudaErrorInvalidValue) return SK_EINVAL;
+  if (e == cudaSuccess) e = sk::upload_plan(b->plan, &b->arena, st);
+  if (e != cudaSuccess) return to_status(e);
   b->planned = true;
   return SK_OK;
 }
 
-// The two launches of a batch run (counted by the caller).
 cudaError_t batch_launch(sk_batch* b, cudaStream_t st) {
-  using namespace sk;
-  const LeftSched sc = device_sched(b->hs, b->d_buf, b->d_status);
-  cudaError_t e = launch_left<kMixed, true>(sc, b->units, st);
-  if (e != cudaSuccess) return e;
-  return splitk_reduce_batched(
-      reinterpret_cast<const ReduceDesc*>(static_cast<uint8_t*>(b->d_buf) + b->off_red),
-      static_cast<int>(b->red.size()), b->max_elems, st);
+  return sk::launch_plan(b->plan, b->arena, st);
 }
 
 sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
@@ -1535,10 +1611,11 @@ sk_status sk_batch_create(sk_batch_handle* out) {
   sk_batch* b = new (std::nothrow) sk_batch;
   if (!b) return SK_ENOMEM;
   cudaError_t e = cudaGetDevice(&b->device);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int) * 4);
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&b->arena.d_status), sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(b->arena.d_status, 0, sizeof(int) * 4);
   if (e != cudaSuccess) {
-    if (b->d_status) cudaFree(b->d_status);
+    if (b->arena.d_status) cudaFree(b->arena.d_status);
     delete b;
     return to_status(e);
   }
@@ -1558,7 +1635,7 @@ sk_status sk_batch_add(sk_batch_handle b, sk_handle h, const float* A, int64_t m
   s.L = m;
   const sk_status st = sk::tc_check(s, A, lda, Y, ldy);
   if (st != SK_OK) return st;
-  sk_batch::Entry e{h->seed, h->dist, h->k, h->scale, A, m, n, lda, Y, ldy};
+  sk::BatchMember e{h->seed, h->dist, h->k, h->scale, A, m, n, lda, Y, ldy, nullptr, 0};
   b->entries.push_back(e);
   batch_invalidate(b);
   return SK_OK;
@@ -1618,8 +1695,9 @@ sk_status sk_batch_status(sk_batch_handle b, void* stream) {
   if (!b) return SK_EINVAL;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   int word = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(&word, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && word != 0) e = cudaMemset(b->d_status, 0, sizeof(int) * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&word, b->arena.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(b->arena.d_status, 0, sizeof(int) * 4);
   if (e != cudaSuccess) return to_status(e);
   return static_cast<sk_status>(word);
 }
@@ -1633,9 +1711,9 @@ sk_status sk_batch_size(sk_batch_handle b, int64_t* count) {
 sk_status sk_batch_destroy(sk_batch_handle b) {
   if (!b) return SK_EINVAL;
   batch_invalidate(b);
-  if (b->d_buf) cudaFree(b->d_buf);
-  if (b->ws) cudaFree(b->ws);
-  if (b->d_status) cudaFree(b->d_status);
+  if (b->arena.d_buf) cudaFree(b->arena.d_buf);
+  if (b->arena.ws) cudaFree(b->arena.ws);
+  if (b->arena.d_status) cudaFree(b->arena.d_status);
   delete b;
   return SK_OK;
 }

@@ -83,6 +83,31 @@ def batched_problems(count: int = 256, m_lo: int = 1024, m_hi: int = 65536, n_lo
     return out
 
 
+@dataclass(frozen=True)
+class Request:
+    arrival_s: float   # offset from the start of the stream
+    prob: Problem
+    row0: int          # first row of the request's A inside the shared source matrix
+
+
+def serving_requests(count: int = 20000, rate: float = 2000.0, m_lo: int = 1024,
+                     m_hi: int = 1 << 18, src_rows: int = 1 << 18, seed: int = 3000
+                     ) -> list[Request]:
+    """A Poisson stream of left-sketch requests: exponential gaps of mean
+    1/rate, shapes drawn as batched_problems (m up to m_hi), and for each a
+    random row window of a shared source matrix of src_rows rows."""
+    probs = batched_problems(count, m_lo=m_lo, m_hi=m_hi, seed=seed)
+    g = _gen("cpu", seed + 1)
+    gaps = torch.empty(count, dtype=torch.float64).exponential_(rate, generator=g)
+    arrivals = torch.cumsum(gaps, 0) - gaps[0]
+    u = torch.rand(count, generator=g, dtype=torch.float64)
+    out = []
+    for i, p in enumerate(probs):
+        row0 = int(float(u[i]) * (src_rows - p.m + 1))
+        out.append(Request(arrival_s=float(arrivals[i]), prob=p, row0=min(row0, src_rows - p.m)))
+    return out
+
+
 CONFIGS = {
     "C1": dict(side="left", m=4096, n=256, k=64, dists=(0,), a_seed=A_SEED, s_seed=S_SEED),
     "C2": dict(side="left", m=1 << 20, n=512, k=2048, dists=(1, 0), a_seed=A_SEED,
