@@ -81,14 +81,17 @@ struct BatchMember {
   int64_t m, n, lda;
   float* Y;
   int64_t ldy;
-  float* part = nullptr;  // own split partials (batch_member_workspace bytes), or null
-  int64_t item_stages = 0;  // own work-item length in stages of 16 rows, or 0
+  // own workspace of batch_member_workspace bytes (the BF16 split of A, then
+  // the split partials), or null for one from the arena
+  void* ws = nullptr;
+  int64_t item_stages = 0;   // own work-item length in stages of 16 rows, or 0
+  bool split_ready = false;  // ws already holds the BF16 split of A (A is not read)
 };
 // Device buffers one batch launch uses; grown on demand, owned by the caller.
 struct BatchArena {
   void* d_buf = nullptr;  // work list + reduce descriptors
   size_t d_bytes = 0;
-  void* ws = nullptr;     // split partials of the members without their own
+  void* ws = nullptr;     // workspaces of the members without their own
   size_t ws_bytes = 0;
   int* d_status = nullptr;
   // pinned staging of the work list: when set, uploads do not synchronise
@@ -101,8 +104,16 @@ struct BatchArena {
 // CTA pairs of the GPU when it runs alone (items of at least 64 stages); a
 // function of the shape only.
 int64_t spread_item_stages(const BatchMember& mb);
-// Bytes of partials a member needs with items of `item_stages` stages.
+// Bytes of workspace a member needs with items of `item_stages` stages.
 size_t batch_member_workspace(const BatchMember& mb, int64_t item_stages);
+// The BF16 split of a left sketch's A[m x n] at the start of its workspace:
+// hi rows of split_ld(n) elements, then lo rows (split_bytes in total).
+int64_t split_ld(int64_t n);
+size_t split_bytes(int64_t m, int64_t n);
+// Write the split of A (any alignment, row stride lds; a device address) into
+// `H` on `st` (one kernel launch).
+cudaError_t split_rows(const float* A, int64_t lds, int64_t m, int64_t n, void* H,
+                       cudaStream_t st);
 // Plan the members (items of about `item_stages` stages), upload the work
 // list into `arena` on `st` (synchronising `st`), make `st` wait for
 // `ready` (may be null) and launch the persistent sketch kernel and the

@@ -109,7 +109,10 @@ struct Request {
   int64_t src_ld = 0;
   cudaEvent_t src_ready = nullptr;  // recorded on the producer's stream at submission
   int64_t ldp = 0;          // row stride of the pool copies of A and Y
-  uint64_t a_bytes = 0, part_bytes = 0, work_bytes = 0, y_bytes = 0;
+  // work block: [copy of A (a_bytes; none when a BF16 request is split
+  // straight from its source)][workspace (ws_bytes): the BF16 split and the
+  // partials, or the SIMT partials]
+  uint64_t a_bytes = 0, ws_bytes = 0, work_bytes = 0, y_bytes = 0;
   uint64_t work_off = 0, y_off = 0;
   bool has_work = false, has_y = false;
   State state = State::Pending;
@@ -126,6 +129,7 @@ struct AdmitCopy {
   const float* src;      // as submitted
   const float* src_dev;  // device-accessible address of src, or null (pageable host)
   int64_t lds, m, n;
+  void* split;           // non-null: write the BF16 split here instead of copying A
   cudaEvent_t ready;     // the producer's event, returned to the free list after use
 };
 
@@ -134,7 +138,8 @@ struct StepItem {
   int64_t ticket;
   sk::BatchMember mb;
   int prec;
-  uint64_t part_bytes;
+  float* simt_part;
+  uint64_t simt_bytes;
 };
 
 struct Lane {
@@ -209,6 +214,7 @@ __global__ void k_admit_copy(const float* __restrict__ src, int64_t lds,
 cudaError_t sk_server::issue_copy(const AdmitCopy& c) {
   const cudaError_t we = cudaStreamWaitEvent(copy_st, c.ready, 0);
   if (we != cudaSuccess) return we;
+  if (c.split != nullptr) return sk::split_rows(c.src_dev, c.lds, c.m, c.n, c.split, copy_st);
   if (c.src_dev == nullptr)  // pageable host memory: the copy engine stages it
     return cudaMemcpy2DAsync(c.dst, c.ldd * sizeof(float), c.src, c.lds * sizeof(float),
                              c.n * sizeof(float), c.m, cudaMemcpyDefault, copy_st);
@@ -303,17 +309,22 @@ std::vector<AdmitCopy> sk_server::admit_locked() {
     r.work_off = woff;
     r.y_off = yoff;
     r.has_work = r.has_y = true;
-    r.mb.A = reinterpret_cast<const float*>(pool.at(woff));
-    r.mb.part = reinterpret_cast<float*>(pool.at(woff + r.a_bytes));
+    void* wsp = pool.at(woff + r.a_bytes);
+    r.mb.A = r.a_bytes ? reinterpret_cast<const float*>(pool.at(woff)) : nullptr;
     r.mb.Y = reinterpret_cast<float*>(pool.at(yoff));
     r.mb.lda = r.ldp;
     r.mb.ldy = r.ldp;
+    if (r.prec == SK_BF16X2) {
+      r.mb.ws = wsp;
+      r.mb.split_ready = r.a_bytes == 0;
+    }
     r.state = State::Admitted;
     admitted.push_back(t);
     AdmitCopy c;
     c.ticket = t;
     c.dst = const_cast<float*>(r.mb.A);
     c.ldd = r.ldp;
+    c.split = r.a_bytes == 0 ? wsp : nullptr;
     c.src = r.src;
     c.src_dev = r.src_dev;
     c.lds = r.src_ld;
@@ -337,7 +348,8 @@ std::vector<StepItem> sk_server::take_step_locked(Lane* ln) {
     Request& r = reqs.at(t);
     r.state = State::Running;
     r.t_launch = now;
-    items.push_back({t, r.mb, r.prec, r.part_bytes});
+    items.push_back({t, r.mb, r.prec,
+                     reinterpret_cast<float*>(pool.at(r.work_off + r.a_bytes)), r.ws_bytes});
     ln->tickets.push_back(t);
   }
   admitted.erase(admitted.begin(), admitted.begin() + take);
@@ -375,8 +387,8 @@ cudaError_t sk_server::launch_items(Lane* ln, const std::vector<StepItem>& items
     s.P = it.mb.k;
     s.Q = it.mb.n;
     s.L = it.mb.m;
-    e = sk::simt_sketch(&h, s, it.mb.A, it.mb.lda, it.mb.Y, it.mb.ldy, it.mb.part,
-                        it.part_bytes, ln->st);
+    e = sk::simt_sketch(&h, s, it.mb.A, it.mb.lda, it.mb.Y, it.mb.ldy, it.simt_part,
+                        it.simt_bytes, ln->st);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ln->h_status, ln->arena.d_status, sizeof(int), cudaMemcpyDeviceToHost,
@@ -582,24 +594,8 @@ sk_status sk_server_submit(sk_server_handle s, sk_handle h, const float* A, int6
   sh.P = h->k;
   sh.Q = n;
   sh.L = m;
-  if (r.prec == SK_BF16X2) {
-    // pool addresses are 256-byte aligned and the strides multiples of 4
-    const sk_status cs = sk::tc_check(sh, reinterpret_cast<const float*>(kAlign), r.ldp,
-                                      reinterpret_cast<const float*>(kAlign), r.ldp);
-    if (cs != SK_OK) return cs;
-    // items sized so that a request alone spreads over the whole GPU; the
-    // length depends on the request's shape only
-    r.mb.item_stages = sk::spread_item_stages(r.mb);
-    r.part_bytes = sk::batch_member_workspace(r.mb, r.mb.item_stages);
-  } else {
-    r.part_bytes = sk::simt_workspace_bytes(sh);
-  }
-  r.a_bytes = round_up(static_cast<uint64_t>(m) * r.ldp * sizeof(float), kAlign);
-  r.work_bytes = r.a_bytes + round_up(r.part_bytes, kAlign);
-  r.y_bytes = round_up(static_cast<uint64_t>(h->k) * r.ldp * sizeof(float), kAlign);
-  r.t_arrival = arrival;
   // device memory, managed memory and mapped pinned host memory are read by
-  // the admission kernel; anything else goes through the copy engine
+  // the admission kernels; anything else goes through the copy engine
   cudaPointerAttributes pa;
   if (cudaPointerGetAttributes(&pa, A) == cudaSuccess) {
     if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged ||
@@ -611,6 +607,25 @@ sk_status sk_server_submit(sk_server_handle s, sk_handle h, const float* A, int6
   } else {
     cudaGetLastError();
   }
+  const uint64_t a_copy = round_up(static_cast<uint64_t>(m) * r.ldp * sizeof(float), kAlign);
+  if (r.prec == SK_BF16X2) {
+    // pool addresses are 256-byte aligned and the strides multiples of 4
+    const sk_status cs = sk::tc_check(sh, reinterpret_cast<const float*>(kAlign), r.ldp,
+                                      reinterpret_cast<const float*>(kAlign), r.ldp);
+    if (cs != SK_OK) return cs;
+    // items sized so that a request alone spreads over the whole GPU; the
+    // length depends on the request's shape only
+    r.mb.item_stages = sk::spread_item_stages(r.mb);
+    r.ws_bytes = round_up(sk::batch_member_workspace(r.mb, r.mb.item_stages), kAlign);
+    // a readable source is split on admission; a pageable one is copied first
+    r.a_bytes = r.src_dev ? 0 : a_copy;
+  } else {
+    r.ws_bytes = round_up(sk::simt_workspace_bytes(sh), kAlign);
+    r.a_bytes = a_copy;
+  }
+  r.work_bytes = r.a_bytes + r.ws_bytes;
+  r.y_bytes = round_up(static_cast<uint64_t>(h->k) * r.ldp * sizeof(float), kAlign);
+  r.t_arrival = arrival;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->stop) return SK_ECANCELLED;
   if (r.work_bytes + r.y_bytes > s->pool.size()) return SK_EBUDGET;

@@ -7,17 +7,18 @@
 // the kernel instead of read (Sec. 6.2's "generate rather than communicate",
 // with shared memory in the role of the processor's local memory).
 //
-// Shared-memory bandwidth, not the tensor core, bounds this product: every
-// stage the MMA re-reads its operands from shared memory while the FP32 A
-// tile is written by TMA, read back and written again as BF16 hi / lo.  A CTA
-// pair (cta_group::2) halves that traffic per SM: one MMA of M = 256 spans
-// both SMs, each CTA supplying 128 rows of S and half of the B (= A tile)
-// rows, so each CTA loads and converts only half of every A tile.
+// Two passes.  The split pass (k_split_bf16x2, HBM-bound) writes
+// hi = bf16(a) and lo = bf16(a - hi) of A once, row-major with rows padded to
+// 64 columns; every 256-row tile of Y then reads the BF16 halves instead of
+// converting the FP32 tile again (with k = 2048 the fused conversion was
+// repeated by 8 tiles and cost more than the split pass).  The sketch kernel
+// keeps S in shared memory only:
 //
 // A pair owns a 256 x NT tile of Y (NT <= 512 TMEM columns in each CTA) and
 // one contiguous range of the contracted dimension m (deterministic split-K):
-//   warp 0       TMA producer: this CTA's FP32 columns of each A tile
-//                [16 rows of m] into a staging ring;
+//   warp 0       TMA producer: one 4D box per stage brings this CTA's
+//                columns of the hi and lo tiles [16 rows of m] into the
+//                operand ring, MN-major with the 128-byte swizzle;
 //   warp 1       TMEM allocation (collective over the pair); in the even CTA
 //                the MMA issuer: per stage 2 passes (hi, lo) x NT/256
 //                tcgen05.mma kind::f16 (M=256, K=16) into the FP32
@@ -25,11 +26,11 @@
 //   warps 2-9    epilogue: every CHAIN stages the accumulator is read out of
 //                this CTA's TMEM and added into its FP32 partial in global
 //                memory (store for the first chain, red.add after);
-//   warps 10-25  workers, in 4 groups that take turns on successive stages
-//                (so that four stages are in flight): generate this CTA's
-//                BF16 S tile [128 x 16] (Philox4x32-10 + Box-Muller, or sign
-//                bits) and convert its A columns into hi = bf16(a),
-//                lo = bf16(a - hi) in the K-major no-swizzle operand layout.
+//   warps 10-25  workers, in 4 groups that take turns on successive stages:
+//                generate this CTA's BF16 S tile [128 x 16] (Philox4x32-10 +
+//                Box-Muller, or sign bits) in the K-major no-swizzle layout,
+//                then pass the stage on to the MMA issuer once this CTA's
+//                hi / lo tile has landed.
 // With k <= 128 a single CTA (cta_group::1, M = 128) does the same alone.
 // The tensor core accumulates in FP32 without round-to-nearest on every
 // add, so its error grows with the chain length; restarting the TMEM chain
@@ -62,9 +63,13 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;       // generated rows per CTA
-constexpr int BK = 16;        // contracted length per stage (MMA K)
+constexpr int BK = 16;        // MMA K; contracted length per stage of the right kernel
+constexpr int LK = 32;        // contracted length per stage of the left kernel
+constexpr int KSTEPS = LK / BK;  // MMA K steps per left stage
 constexpr int NT_MAX = 512;   // output columns per tile (TMEM columns)
-constexpr int CHAIN = 128;    // stages per TMEM accumulation chain
+constexpr int CHAIN = 128;    // MMA K steps per TMEM accumulation chain (2048 rows)
+constexpr int CHAIN_L = CHAIN / KSTEPS;  // left stages per chain
+constexpr int HCHUNK = 64;    // columns of one 128-byte swizzle atom of the split A
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_WORK_WARPS = 16;
 
@@ -75,37 +80,30 @@ constexpr int WARP_WORK0 = WARP_EPI0 + NUM_EPI_WARPS;
 constexpr int NWORK = 32 * NUM_WORK_WARPS;
 constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 
-// Per-CTA buffers.  A CTA of a pair holds NT/2 columns of each A tile.
+// Per-CTA buffers of the left kernel.  A CTA of a pair holds NT/2 columns of
+// each split A tile.
 template <bool PAIR>
 struct Cfg {
-  static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // A columns per CTA
+  static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // most A columns per CTA
   // Worker groups take turns on successive stages.  A group that starts
   // stage s has finished stage s - NGROUPS, so waits never run more than one
   // barrier phase ahead (the parity test would alias) as long as
-  // NGROUPS <= NSF and NGROUPS <= NSO.
+  // NGROUPS <= NSO.
   static constexpr int NGROUPS = PAIR ? 4 : 2;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-#ifndef SK_TC_NSF
-  static constexpr int NSF = PAIR ? 6 : 3;                  // FP32 staging stages
-  static constexpr int NSO = PAIR ? 6 : 3;                  // operand stages
-#else
-  static constexpr int NSF = PAIR ? SK_TC_NSF : 3;
-  static constexpr int NSO = PAIR ? SK_TC_NSO : 3;
-#endif
-  static constexpr uint32_t STAGE_F = BK * COLS * 4;        // FP32 staging
-  static constexpr uint32_t OPB = COLS * BK * 2;            // hi or lo operand
-  static constexpr uint32_t OPS = BM * BK * 2;              // S tile
-  static constexpr uint32_t OFF_F = 0;
-  static constexpr uint32_t OFF_BHI = OFF_F + NSF * STAGE_F;
-  static constexpr uint32_t OFF_BLO = OFF_BHI + NSO * OPB;
-  static constexpr uint32_t OFF_S = OFF_BLO + NSO * OPB;
+  static constexpr int NSO = PAIR ? 5 : 3;                  // operand stages
+  static constexpr uint32_t OPB = 2u * COLS * LK * 2u;      // hi and lo tiles of a stage
+  static constexpr uint32_t OPS = BM * LK * 2;              // S tile: KSTEPS slabs of 16
+  static constexpr uint32_t OFF_B = 0;
+  static constexpr uint32_t OFF_S = OFF_B + NSO * OPB;
   static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
-  static constexpr uint32_t NUM_BARS = 2 * NSF + 2 * NSO + 3;
+  static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
-  static_assert(NGROUPS <= NSF && NGROUPS <= NSO, "worker groups vs ring depth");
+  static_assert(NGROUPS <= NSO, "worker groups vs ring depth");
+  static_assert(OPB % 1024 == 0, "split tiles start on swizzle-atom boundaries");
 };
 
 // K-major no-swizzle operand layout (16-element K slab): core matrix
@@ -115,15 +113,23 @@ __device__ __forceinline__ uint32_t kmaj_off(uint32_t row, uint32_t khalf) {
 }
 constexpr uint32_t LBO = 128;  // K-adjacent core matrices
 constexpr uint32_t SBO = 256;  // 8-row groups
+// The S tile of a stage: KSTEPS K-major slabs [128 rows][16] of 4 KB.
+constexpr uint32_t S_SLAB = BM * BK * 2;
+// MN-major 128-byte-swizzled split A tile as the TMA box lays it out:
+// [hi/lo][64-column chunk][32 rows][64 columns]; atoms of 8 rows x 128 B.
+constexpr uint32_t HCHUNK_BYTES = LK * HCHUNK * 2;  // 4096: one chunk of one stage
+constexpr uint32_t B_LBO = HCHUNK_BYTES;            // next 64 columns
+constexpr uint32_t B_SBO = 8 * HCHUNK * 2;          // 1024: next 8 rows of m
+constexpr uint32_t B_KSTEP = BK * HCHUNK * 2;       // 2048: next 16 rows of m
 
 // One left-sketch problem of a launch (a single sketch, or one member of a
 // batch).  Lives in device memory; the tensor map must be 64-byte aligned.
 struct alignas(128) LeftProblem {
-  CUtensorMap map;  // A[m x n] (n innermost), box {boxw, 16}
+  CUtensorMap map;  // split A: {64 columns, m rows, chunks, hi/lo}, box {64, 16, cols/64, 2}
   float* part;      // partials [splits][P][Q] of this problem
   int64_t P, Q, L;  // P = k, Q = n, L = m
-  int64_t chunk;    // contracted length per split (multiple of BK)
-  int nt;           // output columns per tile: multiple of 16 up to 256, or 512
+  int64_t chunk;    // contracted length per split (multiple of LK)
+  int nt;           // output columns per tile: a multiple of 128 (pairs) or 64 up to 256, or 512
   int dist;         // sk_dist of S
   PhiloxKey key;
 };
@@ -158,6 +164,97 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64
   }
 }
 
+// ---- split pass: A (FP32) -> hi / lo (BF16), rows padded to 64 columns ----
+
+// One matrix of the split pass.  hi row r at H + r*ldh, lo row r at
+// H + part + r*ldh; columns n .. ldh-1 are written as zeros.
+struct SplitDesc {
+  const float* A;
+  int64_t lda;
+  __nv_bfloat16* H;
+  int64_t ldh, part;
+  int64_t m, n;
+};
+
+// Store hi / lo of the values a[0..7] of columns c .. c+7 of row r.
+__device__ __forceinline__ void split_store(const SplitDesc& d, int64_t r, int64_t c,
+                                            const float (&a)[8]) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
+    const float h0 = __uint_as_float(hw[e] << 16);
+    const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
+    lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
+  }
+  __nv_bfloat16* dst = d.H + r * d.ldh + c;
+  *reinterpret_cast<uint4*>(dst) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(dst + d.part) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// Columns c .. c+7 of row r (c a multiple of 8; rows 16-byte aligned).
+__device__ __forceinline__ void split_group(const SplitDesc& d, int64_t r, int64_t c) {
+  float a[8];
+  const float* src = d.A + r * d.lda + c;
+  if (c + 8 <= d.n) {
+    const float4 v0 = __ldcs(reinterpret_cast<const float4*>(src));
+    const float4 v1 = __ldcs(reinterpret_cast<const float4*>(src + 4));
+    a[0] = v0.x; a[1] = v0.y; a[2] = v0.z; a[3] = v0.w;
+    a[4] = v1.x; a[5] = v1.y; a[6] = v1.z; a[7] = v1.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a[e] = c + e < d.n ? __ldcs(src + e) : 0.0f;
+  }
+  split_store(d, r, c, a);
+}
+
+// One warp per row with 4-byte loads: rows of any alignment (the serving
+// path reads requests straight from their sources).
+__global__ void __launch_bounds__(256) k_split_rows(const SplitDesc d) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); r < d.m;
+       r += warps) {
+    const float* src = d.A + r * d.lda;
+    for (int64_t c = 8 * lane; c < d.ldh; c += 256) {
+      float a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a[e] = c + e < d.n ? src[c + e] : 0.0f;
+      split_store(d, r, c, a);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_split_bf16x2_one(const SplitDesc d) {
+  const int64_t gpr = d.ldh / 8;
+  const int64_t total = d.m * gpr;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    split_group(d, t / gpr, (t % gpr) * 8);
+}
+
+// Many matrices in one launch: prefix[i] = groups of 8 columns before
+// matrix i (prefix[count] = total).
+__global__ void __launch_bounds__(256)
+    k_split_bf16x2_many(const SplitDesc* ds, const int64_t* prefix, int count) {
+  const int64_t total = prefix[count];
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last i with prefix[i] <= t
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const SplitDesc d = ds[lo];
+    const int64_t u = t - prefix[lo];
+    const int64_t gpr = d.ldh / 8;
+    split_group(d, u / gpr, (u % gpr) * 8);
+  }
+}
+
 // Per-item geometry shared by every role.
 struct ItemGeo {
   const LeftProblem* pr;
@@ -180,28 +277,28 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
   g.q0 = static_cast<int64_t>(it.tq) * g.nt;
   g.lbeg = static_cast<int64_t>(it.z) * g.pr->chunk;
   g.lend = min(g.pr->L, g.lbeg + g.pr->chunk);
-  g.nsteps = static_cast<int>((g.lend - g.lbeg + BK - 1) / BK);
+  g.nsteps = static_cast<int>((g.lend - g.lbeg + LK - 1) / LK);
   return g;
 }
 
-// Generate this CTA's BF16 S tile [128 x 16] of one stage.  Rademacher tasks
-// keep their Philox words across the 8 stages one call covers.
+// Generate this CTA's BF16 S tile [128 x 32] of one stage (two K-major slabs
+// of 16 columns).  A Rademacher task is one row of the stage: one 32-bit
+// Philox word, kept across the four stages one call covers.  Gaussian and
+// uniform tasks are four entries of one row (one Philox call).
 template <int DIST, class C>
 __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64_t cbase, int wt,
                                           uint32_t* cached_blk, uint4* words) {
   if (DIST == kRademacher) {
-    constexpr int RAD_IT = (2 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    constexpr int RAD_IT = (BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
     for (int it = 0; it < RAD_IT; ++it) {
       const int t = wt + it * C::GROUP_THREADS;
-      if (t >= 2 * BM) break;
-      const uint32_t r = static_cast<uint32_t>(t & (BM - 1));
-      const uint32_t hh = static_cast<uint32_t>(t >> 7);
+      if (t >= BM) break;
+      const uint32_t r = static_cast<uint32_t>(t);
       const int64_t grow = g.p0 + r;
-      const int64_t c0 = cbase + 8 * hh;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (grow < g.pr->P && c0 < g.lend) {
-        const uint32_t c = static_cast<uint32_t>(c0);
+      uint32_t bits = 0u, valid = 0u;
+      if (grow < g.pr->P && cbase < g.lend) {
+        const uint32_t c = static_cast<uint32_t>(cbase);  // a multiple of 32
         const uint32_t blk = c >> 7;
         if (blk != cached_blk[it]) {
           words[it] = rademacher_bits(g.pr->key, static_cast<uint32_t>(grow), blk, 0u);
@@ -209,29 +306,46 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
         }
         const uint32_t wsel = (c >> 5) & 3u;
         const uint4 wv = words[it];
-        const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
-        const uint32_t bits = w >> (c & 31u);
-        // +1.0 = 0x3F80, -1.0 = 0xBF80: the sign bit carries the random bit
-        v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
-        v.y = 0x3F803F80u | ((bits & 4u) << 13) | ((bits & 8u) << 28);
-        v.z = 0x3F803F80u | ((bits & 16u) << 11) | ((bits & 32u) << 26);
-        v.w = 0x3F803F80u | ((bits & 64u) << 9) | ((bits & 128u) << 24);
+        bits = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
+        const int64_t nv = g.lend - cbase;
+        valid = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
       }
-      *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // 8 columns each: slab j / 2, half j % 2
+        const uint32_t b = bits >> (8 * j);
+        const uint32_t vm = valid >> (8 * j);
+        uint4 v;
+        // +1.0 = 0x3F80, -1.0 = 0xBF80: the sign bit carries the random bit
+        v.x = 0x3F803F80u | ((b & 1u) << 15) | ((b & 2u) << 30);
+        v.y = 0x3F803F80u | ((b & 4u) << 13) | ((b & 8u) << 28);
+        v.z = 0x3F803F80u | ((b & 16u) << 11) | ((b & 32u) << 26);
+        v.w = 0x3F803F80u | ((b & 64u) << 9) | ((b & 128u) << 24);
+        if ((vm & 0xffu) != 0xffu) {  // columns past the end of the split are zero
+          v.x &= ((vm & 1u) ? 0x0000ffffu : 0u) | ((vm & 2u) ? 0xffff0000u : 0u);
+          v.y &= ((vm & 4u) ? 0x0000ffffu : 0u) | ((vm & 8u) ? 0xffff0000u : 0u);
+          v.z &= ((vm & 16u) ? 0x0000ffffu : 0u) | ((vm & 32u) ? 0xffff0000u : 0u);
+          v.w &= ((vm & 64u) ? 0x0000ffffu : 0u) | ((vm & 128u) ? 0xffff0000u : 0u);
+        }
+        *reinterpret_cast<uint4*>(sdst + (j >> 1) * S_SLAB +
+                                  kmaj_off(r, static_cast<uint32_t>(j & 1))) = v;
+      }
     }
   } else {
-    // 8 rows x 4 quads per 32 tasks, 4 entries (one Philox call) each; a
-    // fixed, unrolled count per thread lets independent chains interleave
-    constexpr int GEN_IT = (4 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    // per 32 tasks: 8 rows x 4 quads of one slab, 4 entries (one Philox call)
+    // each; a fixed, unrolled count per thread lets independent chains
+    // interleave
+    constexpr int GEN_IT = (8 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
     for (int it = 0; it < GEN_IT; ++it) {
       const int t = wt + it * C::GROUP_THREADS;
-      if (t >= 4 * BM) break;
+      if (t >= 8 * BM) break;
       const uint32_t l = static_cast<uint32_t>(t & 31);
-      const uint32_t r = static_cast<uint32_t>(t >> 5) * 8u + (l >> 2);
+      const uint32_t w = static_cast<uint32_t>(t >> 5);
+      const uint32_t slab = w >> 4;
+      const uint32_t r = (w & 15u) * 8u + (l >> 2);
       const uint32_t qd = l & 3u;
       const int64_t grow = g.p0 + r;
-      const int64_t c0 = cbase + 4 * qd;
+      const int64_t c0 = cbase + 16 * slab + 4 * qd;
       uint2 v = make_uint2(0u, 0u);
       if (grow < g.pr->P && c0 < g.lend) {
         const uint32_t c = static_cast<uint32_t>(c0);
@@ -240,40 +354,8 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
                              : gaussian4(g.pr->key, static_cast<uint32_t>(grow), c >> 2, 0u);
         v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
       }
-      *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
+      *reinterpret_cast<uint2*>(sdst + slab * S_SLAB + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
     }
-  }
-}
-
-// Split this CTA's FP32 A columns of one stage (staging: boxes of <= 256
-// columns x 16 rows) into BF16 hi / lo operand rows (row j = column j).
-template <class C>
-__device__ __forceinline__ void convert_stage(const float* stg, uint8_t* bhi, uint8_t* blo,
-                                              int cols, int wt) {
-  constexpr int CONV_IT = (2 * C::COLS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
-#pragma unroll
-  for (int it = 0; it < CONV_IT; ++it) {
-    const int i = wt + it * C::GROUP_THREADS;
-    if (i >= 2 * cols) break;
-    const int hh = i >= cols ? 1 : 0;
-    const int j = i - hh * cols;
-    const int box = j >> 8;
-    const int bw = min(cols - box * 256, 256);
-    const float* src = stg + box * 256 * BK + (8 * hh) * bw + (j - box * 256);
-    float a[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) a[e] = src[e * bw];
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
-      const float h0 = __uint_as_float(hw[e] << 16);
-      const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
-      lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
-    }
-    const uint32_t o = kmaj_off(static_cast<uint32_t>(j), static_cast<uint32_t>(hh));
-    *reinterpret_cast<uint4*>(bhi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4*>(blo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
@@ -292,11 +374,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                              ~static_cast<uintptr_t>(1023));
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = sbase + C::OFF_BAR;
-  auto full_f = [&](int i) { return bar0 + 8u * i; };
-  auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
-  auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
-  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 2 * C::NSO);
+  // full_b: this CTA's split A tile has landed; full_o (even CTA): both CTAs'
+  // operands of the stage are ready; empty_o: the MMAs that read the slot
+  // have completed (signalled to both CTAs)
+  auto full_b = [&](int i) { return bar0 + 8u * i; };
+  auto full_o = [&](int i) { return bar0 + 8u * (C::NSO + i); };
+  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (3 * C::NSO);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
@@ -311,11 +395,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int ie = sc.begin[unit + 1];
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < C::NSF; ++i) {
-      mbar_init(full_f(i), 1);
-      mbar_init(empty_f(i), C::GROUP_WARPS);
-    }
     for (int i = 0; i < C::NSO; ++i) {
+      mbar_init(full_b(i), 1);
       mbar_init(full_o(i), C::GROUP_WARPS * (PAIR ? 2 : 1));  // one worker group of each CTA
       mbar_init(empty_o(i), 1);
     }
@@ -352,22 +433,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const CUtensorMap* map = &ig.pr->map;
         tma_prefetch_desc(map);
-        const uint32_t tx = static_cast<uint32_t>(ig.cols * BK * 4);
-        const int64_t x0 = ig.q0 + static_cast<int64_t>(rank) * ig.cols;
+        const uint32_t tx = static_cast<uint32_t>(2 * ig.cols * LK * 2);  // hi + lo
+        const int32_t z0 =
+            static_cast<int32_t>((ig.q0 + static_cast<int64_t>(rank) * ig.cols) / HCHUNK);
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
-          const int sf = g % C::NSF;
-          if (g >= C::NSF && !mbar_wait(empty_f(sf), ((g / C::NSF) & 1) ^ 1, ab, 0x11, g)) break;
-          mbar_arrive_expect_tx(full_f(sf), tx);
-          const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * BK);
-          for (int b = 0; b * 256 < ig.cols; ++b)
-            tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F + static_cast<uint32_t>(b * 256 * BK * 4),
-                        map, static_cast<int32_t>(x0 + b * 256), y, full_f(sf));
+          const int so = g % C::NSO;
+          // the MMAs that read this slot last time have completed
+          if (g >= C::NSO && !mbar_wait(empty_o(so), ((g / C::NSO) & 1) ^ 1, ab, 0x13, g)) break;
+          mbar_arrive_expect_tx(full_b(so), tx);
+          const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * LK);
+          tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
           issued = g + 1;
         }
       }
       if (*abort_flag) {  // let the copies already issued land before leaving
-        for (int t = max(0, issued - C::NSF); t < issued; ++t)
-          drain_wait(full_f(t % C::NSF), (t / C::NSF) & 1, 100000000ull);
+        for (int t = max(0, issued - C::NSO); t < issued; ++t)
+          drain_wait(full_b(t % C::NSO), (t / C::NSO) & 1, 100000000ull);
       }
     }
   } else if (warp == WARP_MMA) {
@@ -376,10 +457,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool stop = false;
       for (int idx = ib; idx < ie && !stop; ++idx) {
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
-        const uint32_t idesc = idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh));
+        const uint32_t idesc =
+            idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
+        const uint32_t pstride = static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
+        const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * HCHUNK_BYTES;
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
-          const int in_chain = s % CHAIN;
+          const int in_chain = s % CHAIN_L;
           // a new chain may start only after every epilogue has read the last one
           if (in_chain == 0 && gc > 0 && !mbar_wait(acc_empty, (gc - 1) & 1, ab, 0x25, gc)) {
             stop = true;
@@ -390,21 +474,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint64_t adesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
+          const uint32_t sslot = sbase + C::OFF_S + so * C::OPS;
+          const uint32_t bslot = sbase + C::OFF_B + so * C::OPB;
 #pragma unroll
-          for (int pass = 0; pass < 2; ++pass) {
-            const uint32_t bb = sbase + (pass ? C::OFF_BLO : C::OFF_BHI) + so * C::OPB;
-            for (int h = 0; h < ig.nmma; ++h) {
-              const uint64_t bdesc =
-                  smem_desc(bb + static_cast<uint32_t>(h * ig.bh / 8) * SBO, LBO, SBO);
-              const uint32_t acc = (in_chain > 0 || pass > 0) ? 1u : 0u;
-              if (PAIR)
-                mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
-              else
-                mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+          for (int ks = 0; ks < KSTEPS; ++ks) {
+            const uint64_t adesc = smem_desc(sslot + ks * S_SLAB, LBO, SBO);
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+              for (int h = 0; h < ig.nmma; ++h) {
+                const uint64_t bdesc = smem_desc_sw128(
+                    bslot + static_cast<uint32_t>(pass) * pstride +
+                        static_cast<uint32_t>(h) * hstride + ks * B_KSTEP,
+                    B_LBO, B_SBO);
+                const uint32_t acc = (in_chain > 0 || ks > 0 || pass > 0) ? 1u : 0u;
+                if (PAIR)
+                  mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+                else
+                  mma_bf16(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
+              }
             }
           }
-          const bool chain_end = in_chain == CHAIN - 1 || s == ig.nsteps - 1;
+          const bool chain_end = in_chain == CHAIN_L - 1 || s == ig.nsteps - 1;
           if (PAIR) {  // operands and accumulator are both CTAs'
             mma_commit_pair_both(empty_o(so));
             if (chain_end) mma_commit_pair_both(acc_full);
@@ -436,7 +526,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t P = ig.pr->P, Q = ig.pr->Q;
       float* dst_row = ig.pr->part + (static_cast<int64_t>(it.z) * P + gp) * Q + ig.q0;
       const bool vec_ok = (Q % 4) == 0;
-      const int nchains = (ig.nsteps + CHAIN - 1) / CHAIN;
+      const int nchains = (ig.nsteps + CHAIN_L - 1) / CHAIN_L;
       for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
         const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
         if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
@@ -496,11 +586,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {
-    // ---- workers: generate this CTA's S tile and convert its A columns ----
+    // ---- workers: generate this CTA's S tile, hand the stage to the MMA ----
     // group grp handles the stages g = grp (mod NGROUPS)
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
     const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
-    constexpr int RAD_IT = (2 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    constexpr int RAD_IT = (BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
     uint32_t cached_blk[RAD_IT];
     uint4 words[RAD_IT];
     int g = 0;
@@ -514,16 +604,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       for (int s = 0; s < ig.nsteps; ++s, ++g) {
         if (g % C::NGROUPS != grp) continue;
-        const int sf = g % C::NSF;
         const int so = g % C::NSO;
-        // the MMAs that read operand buffer `so` last time have completed
+        // the MMAs that read S tile `so` last time have completed
         bool ok = g < C::NSO || mbar_wait(empty_o(so), ((g / C::NSO) & 1) ^ 1, ab, 0x43, g);
         if (!__all_sync(0xffffffffu, ok)) {  // leave together (abort path)
           stop = true;
           break;
         }
         uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
-        const int64_t cbase = ig.lbeg + static_cast<int64_t>(s) * BK;
+        const int64_t cbase = ig.lbeg + static_cast<int64_t>(s) * LK;
         if (DIST != kMixed)
           gen_stage<DIST, C>(sdst, ig, cbase, wt, cached_blk, words);
         else if (ig.dist == kRademacher)
@@ -532,26 +621,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
         else
           gen_stage<kGaussian, C>(sdst, ig, cbase, wt, cached_blk, words);
-        // conversion needs this stage's A tile
-        ok = mbar_wait(full_f(sf), (g / C::NSF) & 1, ab, 0x40, g);
+        // this CTA's split A tile of the stage has landed
+        ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x40, g);
         if (!__all_sync(0xffffffffu, ok)) {
           stop = true;
           break;
         }
-        convert_stage<C>(reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F),
-                         smem + C::OFF_BHI + so * C::OPB, smem + C::OFF_BLO + so * C::OPB,
-                         ig.cols, wt);
-        if (PAIR)
-          fence_proxy_async_cluster();  // the even CTA's MMA reads these operands
-        else
-          fence_proxy_async_smem();
+        fence_proxy_async_smem();  // the S tile is read by the tensor core
         __syncwarp();
         if (lane == 0) {
           if (PAIR)
             mbar_arrive_cluster(lead_full_o + 8u * so);
           else
             mbar_arrive(full_o(so));
-          mbar_arrive(empty_f(sf));
         }
       }
     }
@@ -977,7 +1059,7 @@ bool encode_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
 // Geometry of one left problem.
 struct LeftPlan {
   bool pair;
-  int nt, boxw;
+  int nt;
   int64_t tiles_p, tiles_q;  // tiles_p counts pair tiles (256 rows) when pair
   int splits;
   int64_t chunk;
@@ -987,24 +1069,24 @@ struct LeftPlan {
 LeftPlan left_geometry(const GemmShape& s, bool pair) {
   LeftPlan pl;
   pl.pair = pair;
-  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + 15) / 16 * 16);
-  const int cta_cols = pair ? pl.nt / 2 : pl.nt;
-  pl.boxw = cta_cols > 256 ? 256 : cta_cols;
+  // every CTA holds whole 64-column chunks of the split A
+  const int64_t gran = pair ? 2 * HCHUNK : HCHUNK;
+  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + gran - 1) / gran * gran);
   pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
   pl.tiles_p = (s.P + (pair ? 2 * BM : BM) - 1) / (pair ? 2 * BM : BM);
   pl.splits = 1;
-  pl.chunk = (s.L + BK - 1) / BK * BK;
-  pl.steps = pl.chunk / BK;
+  pl.chunk = (s.L + LK - 1) / LK * LK;
+  pl.steps = pl.chunk / LK;
   return pl;
 }
 
 void set_splits(LeftPlan* pl, const GemmShape& s, int64_t splits) {
   if (splits < 1) splits = 1;
   int64_t chunk = (s.L + splits - 1) / splits;
-  chunk = (chunk + BK - 1) / BK * BK;
+  chunk = (chunk + LK - 1) / LK * LK;
   pl->chunk = chunk;
   pl->splits = static_cast<int>((s.L + chunk - 1) / chunk);
-  pl->steps = chunk / BK;
+  pl->steps = chunk / LK;
 }
 
 // A single sketch: pairs when the output has at least two 128-row tiles;
@@ -1015,8 +1097,8 @@ LeftPlan plan_left(const GemmShape& s) {
   LeftPlan pl = left_geometry(s, ps > 0);
   const int64_t units = pl.pair ? ps / 2 : num_sms_tc();
   const int64_t tiles = pl.tiles_p * pl.tiles_q;
-  const int64_t steps_total = (s.L + BK - 1) / BK;
-  int64_t smax = steps_total / 8;  // at least 8 stages per split
+  const int64_t steps_total = (s.L + LK - 1) / LK;
+  int64_t smax = steps_total / 4;  // at least 128 rows per split
   if (smax > 128) smax = 128;
   if (smax < 1) smax = 1;
   int64_t best = 1;
@@ -1033,6 +1115,25 @@ LeftPlan plan_left(const GemmShape& s) {
   }
   set_splits(&pl, s, best);
   return pl;
+}
+
+// Split pass of one sketch (A rows 16-byte aligned, lda a multiple of 4).
+cudaError_t split_launch_one(const float* A, int64_t lda, int64_t m, int64_t n, void* H,
+                             cudaStream_t st) {
+  SplitDesc d;
+  d.A = A;
+  d.lda = lda;
+  d.H = static_cast<__nv_bfloat16*>(H);
+  d.ldh = (n + HCHUNK - 1) / HCHUNK * HCHUNK;
+  d.part = m * d.ldh;
+  d.m = m;
+  d.n = n;
+  const int64_t total = m * (d.ldh / 8);
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256,
+                                           static_cast<int64_t>(num_sms_tc()) * 16);
+  k_split_bf16x2_one<<<static_cast<unsigned>(blocks), 256, 0, st>>>(d);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // Host image of a work list: problems (128-byte aligned), items, per-unit
@@ -1123,10 +1224,28 @@ cudaError_t launch_left_dist(int dist, const LeftSched& sc, int64_t units, cudaS
   return launch_left<kGaussian, PAIR>(sc, units, st);
 }
 
-bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const float* A,
-                  int64_t lda, float* part, uint64_t seed, int dist) {
+// The split A of an m x n problem as a 4D tensor {64 columns, m rows,
+// 64-column chunks, hi/lo}; one box = `cols` columns of 16 rows of both.
+bool encode_split_map(CUtensorMap* map, const void* H, int64_t m, int64_t n, int cols) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const int64_t ldh = split_ld(n);
+  const cuuint64_t gdim[4] = {static_cast<cuuint64_t>(HCHUNK), static_cast<cuuint64_t>(m),
+                              static_cast<cuuint64_t>(ldh / HCHUNK), 2};
+  const cuuint64_t gstride[3] = {static_cast<cuuint64_t>(ldh) * 2, HCHUNK * 2,
+                                 static_cast<cuuint64_t>(m) * static_cast<cuuint64_t>(ldh) * 2};
+  const cuuint32_t box[4] = {static_cast<cuuint32_t>(HCHUNK), static_cast<cuuint32_t>(LK),
+                             static_cast<cuuint32_t>(cols / HCHUNK), 2};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(H), gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
+                  float* part, uint64_t seed, int dist) {
   memset(pr, 0, sizeof(*pr));
-  if (!encode_map(&pr->map, A, s.L, s.Q, lda, pl.boxw, BK)) return false;
+  if (!encode_split_map(&pr->map, H, s.L, s.Q, pl.pair ? pl.nt / 2 : pl.nt)) return false;
   pr->part = part;
   pr->P = s.P;
   pr->Q = s.Q;
@@ -1222,10 +1341,34 @@ cudaError_t grow_device(void** buf, size_t* have, size_t need) {
 
 }  // namespace
 
+int64_t split_ld(int64_t n) { return (n + HCHUNK - 1) / HCHUNK * HCHUNK; }
+
+size_t split_bytes(int64_t m, int64_t n) {
+  return (static_cast<size_t>(m) * static_cast<size_t>(split_ld(n)) * 4 + 255) / 256 * 256;
+}
+
+cudaError_t split_rows(const float* A, int64_t lds, int64_t m, int64_t n, void* H,
+                       cudaStream_t st) {
+  SplitDesc d;
+  d.A = A;
+  d.lda = lds;
+  d.H = static_cast<__nv_bfloat16*>(H);
+  d.ldh = split_ld(n);
+  d.part = m * d.ldh;
+  d.m = m;
+  d.n = n;
+  const int64_t rows_per_block = 256 / 32;
+  const int64_t blocks = std::min<int64_t>((m + rows_per_block - 1) / rows_per_block,
+                                           static_cast<int64_t>(num_sms_tc()) * 8);
+  k_split_rows<<<static_cast<unsigned>(blocks), 256, 0, st>>>(d);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 size_t tc_workspace_bytes(const GemmShape& s) {
   if (s.left) {
     const LeftPlan pl = plan_left(s);
-    return static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
+    return split_bytes(s.L, s.Q) + static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   }
   const Plan pl = plan_right(s);
   return static_cast<size_t>(pl.splits) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
@@ -1279,8 +1422,11 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
                       float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (!s.left) return tc_sketch_right(h, s, A, lda, Y, ldy, ws, ws_bytes, st);
   const LeftPlan pl = plan_left(s);
-  const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
+  const size_t sb = split_bytes(s.L, s.Q);
+  const size_t need = sb + static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
+  void* H = ws;
+  float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + sb);
   sk_sketch* hm = const_cast<sk_sketch*>(h);
   // The work list depends only on these; upload it again only when they change.
   const uint64_t key[8] = {reinterpret_cast<uint64_t>(A), static_cast<uint64_t>(s.L),
@@ -1291,7 +1437,7 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   const int64_t units = pl.pair ? pair_slots() / 2 : num_sms_tc();
   HostSched hs;
   hs.probs.resize(1);
-  if (!fill_problem(&hs.probs[0], pl, s, A, lda, static_cast<float*>(ws), h->seed, h->dist))
+  if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist))
     return cudaErrorInvalidValue;
   build_items(std::vector<LeftPlan>{pl}, units, &hs);
   pack_sched(&hs);
@@ -1304,23 +1450,29 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   }
   const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status);
   const int64_t nunits = static_cast<int64_t>(hs.begin.size()) - 1;
+  // the measurement hook brackets both passes: split of A, then the sketch
   prof_mark(h->prof_start, st);
-  const cudaError_t e = pl.pair ? launch_left_dist<true>(h->dist, sc, nunits, st)
-                                : launch_left_dist<false>(h->dist, sc, nunits, st);
+  cudaError_t e = split_launch_one(A, lda, s.L, s.Q, H, st);
+  if (e != cudaSuccess) return e;
+  e = pl.pair ? launch_left_dist<true>(h->dist, sc, nunits, st)
+              : launch_left_dist<false>(h->dist, sc, nunits, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
   // fixed-order sum of the split partials, times 1/sqrt(k), into Y
-  return splitk_reduce(static_cast<float*>(ws), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+  return splitk_reduce(part, pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
 }
 
 struct PlannedBatch {
   HostSched hs;
   std::vector<ReduceDesc> red;
-  size_t off_red = 0;
-  size_t ws_floats = 0;
+  std::vector<SplitDesc> splits;   // members whose split pass runs in this batch
+  std::vector<int64_t> prefix;     // groups of 8 columns before each of them
+  size_t off_red = 0, off_split = 0, off_prefix = 0, bytes = 0;
+  size_t ws_bytes = 0;             // arena workspace the members need
   int64_t max_elems = 0;
   int64_t units = 0;
+  int launches = 0;                // kernels of one run: split (if any), sketch, reduce
 };
 
 LeftPlan member_plan(const BatchMember& mb, int64_t item_stages, GemmShape* shape) {
@@ -1331,113 +1483,152 @@ LeftPlan member_plan(const BatchMember& mb, int64_t item_stages, GemmShape* shap
   s.Q = mb.n;
   s.L = mb.m;
   LeftPlan pl = left_geometry(s, true);
-  const int64_t steps_total = (s.L + BK - 1) / BK;
-  set_splits(&pl, s, (steps_total + item_stages - 1) / item_stages);
+  const int64_t rows16 = (s.L + 15) / 16;  // item lengths count 16-row units
+  set_splits(&pl, s, (rows16 + item_stages - 1) / item_stages);
   if (shape) *shape = s;
   return pl;
 }
 
-// Work list of a batch whose partials start at `ws`; with `ws` null only the
-// size of the partials (`ws_floats`) is computed.
-bool plan_members(const BatchMember* mbs, size_t count, int64_t item_stages, float* ws,
+size_t partial_bytes(const LeftPlan& pl, const GemmShape& s) {
+  return (static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float) + 255) / 256 * 256;
+}
+
+// Work list of a batch whose arena workspace starts at `arena`; with `arena`
+// null only the arena size (`ws_bytes`) is computed.  A member's workspace
+// holds its BF16 split of A (split_bytes), then its partials.
+bool plan_members(const BatchMember* mbs, size_t count, int64_t item_stages, uint8_t* arena,
                   PlannedBatch* pb) {
   std::vector<LeftPlan> plans;
   std::vector<GemmShape> shapes;
-  std::vector<size_t> part_off;
+  std::vector<size_t> ws_off;
   size_t total = 0;
   for (size_t i = 0; i < count; ++i) {
     GemmShape s;
     plans.push_back(member_plan(mbs[i], item_stages, &s));
     shapes.push_back(s);
-    // every member's partials start on a 256-byte boundary: the epilogue
-    // stores 16-byte vectors when n is a multiple of 4
-    part_off.push_back(total);
-    if (mbs[i].part == nullptr)
-      total += (static_cast<size_t>(plans.back().splits) * s.P * s.Q + 63) / 64 * 64;
+    ws_off.push_back(total);  // 256-byte aligned: partials take 16-byte vector stores
+    if (mbs[i].ws == nullptr) total += split_bytes(s.L, s.Q) + partial_bytes(plans.back(), s);
   }
-  pb->ws_floats = total;
-  if (ws == nullptr) return true;  // sizing pass
+  pb->ws_bytes = total;
+  if (arena == nullptr) return true;  // sizing pass
   pb->hs = HostSched();
   pb->hs.probs.resize(count);
+  pb->red.clear();
+  pb->splits.clear();
+  pb->prefix.assign(1, 0);
+  pb->max_elems = 0;
   for (size_t i = 0; i < count; ++i) {
-    float* part = mbs[i].part ? mbs[i].part : ws + part_off[i];
-    if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], mbs[i].A, mbs[i].lda, part,
-                      mbs[i].seed, mbs[i].dist))
+    const BatchMember& mb = mbs[i];
+    uint8_t* w = mb.ws ? static_cast<uint8_t*>(mb.ws) : arena + ws_off[i];
+    float* part = reinterpret_cast<float*>(w + split_bytes(mb.m, mb.n));
+    if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], w, part, mb.seed, mb.dist))
       return false;
+    if (!mb.split_ready) {
+      SplitDesc d;
+      d.A = mb.A;
+      d.lda = mb.lda;
+      d.H = reinterpret_cast<__nv_bfloat16*>(w);
+      d.ldh = split_ld(mb.n);
+      d.part = mb.m * d.ldh;
+      d.m = mb.m;
+      d.n = mb.n;
+      pb->splits.push_back(d);
+      pb->prefix.push_back(pb->prefix.back() + d.m * (d.ldh / 8));
+    }
+    ReduceDesc r;
+    r.part = part;
+    r.Y = mb.Y;
+    r.P = mb.k;
+    r.Q = mb.n;
+    r.ldy = mb.ldy;
+    r.splits = plans[i].splits;
+    r.scale = mb.scale;
+    pb->red.push_back(r);
+    pb->max_elems = std::max<int64_t>(pb->max_elems, mb.k * mb.n);
   }
   const int64_t slots = pair_slots();
   if (slots <= 0) return false;
   build_items(plans, slots / 2, &pb->hs);
   pack_sched(&pb->hs);
   pb->units = static_cast<int64_t>(pb->hs.begin.size()) - 1;
-  pb->red.clear();
-  pb->max_elems = 0;
-  for (size_t i = 0; i < count; ++i) {
-    ReduceDesc d;
-    d.part = mbs[i].part ? mbs[i].part : ws + part_off[i];
-    d.Y = mbs[i].Y;
-    d.P = mbs[i].k;
-    d.Q = mbs[i].n;
-    d.ldy = mbs[i].ldy;
-    d.splits = plans[i].splits;
-    d.scale = mbs[i].scale;
-    pb->red.push_back(d);
-    pb->max_elems = std::max<int64_t>(pb->max_elems, mbs[i].k * mbs[i].n);
-  }
-  pb->off_red = (pb->hs.bytes + 255) / 256 * 256;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  pb->off_red = up(pb->hs.bytes);
+  pb->off_split = up(pb->off_red + pb->red.size() * sizeof(ReduceDesc));
+  pb->off_prefix = up(pb->off_split + pb->splits.size() * sizeof(SplitDesc));
+  pb->bytes = pb->off_prefix + pb->prefix.size() * sizeof(int64_t);
+  pb->launches = pb->splits.empty() ? 2 : 3;
   return true;
 }
 
-// Plan the members twice: once for the size of the partials, once with the
+// Plan the members twice: once for the size of the arena, once with the
 // arena's workspace in place.
 cudaError_t plan_into_arena(const BatchMember* mbs, size_t count, int64_t item_stages,
                             BatchArena* ar, PlannedBatch* pb) {
   if (!plan_members(mbs, count, item_stages, nullptr, pb)) return cudaErrorInvalidValue;
-  const cudaError_t e = grow_device(&ar->ws, &ar->ws_bytes, pb->ws_floats * sizeof(float) + 256);
+  const cudaError_t e = grow_device(&ar->ws, &ar->ws_bytes, pb->ws_bytes + 256);
   if (e != cudaSuccess) return e;
-  if (!plan_members(mbs, count, item_stages, static_cast<float*>(ar->ws), pb))
+  if (!plan_members(mbs, count, item_stages, static_cast<uint8_t*>(ar->ws), pb))
     return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
-// Copy the work list and the reduce descriptors into the arena; waits for the
-// copies so that the host images may change afterwards.
+// One host image of everything a run reads: work list, reduce descriptors,
+// split descriptors and their prefix sums.
+void pack_plan(const PlannedBatch& pb, uint8_t* h) {
+  memcpy(h, pb.hs.blob.data(), pb.hs.bytes);
+  memcpy(h + pb.off_red, pb.red.data(), pb.red.size() * sizeof(ReduceDesc));
+  if (!pb.splits.empty())
+    memcpy(h + pb.off_split, pb.splits.data(), pb.splits.size() * sizeof(SplitDesc));
+  memcpy(h + pb.off_prefix, pb.prefix.data(), pb.prefix.size() * sizeof(int64_t));
+}
+
+// Copy the plan into the arena.  With async_upload the copy goes through the
+// arena's pinned staging and is not waited for; otherwise this waits for the
+// copy so that the host image may change afterwards.
 cudaError_t upload_plan(const PlannedBatch& pb, BatchArena* ar, cudaStream_t st) {
-  const size_t total = pb.off_red + pb.red.size() * sizeof(ReduceDesc);
-  cudaError_t e = grow_device(&ar->d_buf, &ar->d_bytes, total);
+  cudaError_t e = grow_device(&ar->d_buf, &ar->d_bytes, pb.bytes);
   if (e != cudaSuccess) return e;
   if (ar->async_upload) {
-    if (ar->h_stage_bytes < total) {
+    if (ar->h_stage_bytes < pb.bytes) {
       if (ar->h_stage) cudaFreeHost(ar->h_stage);
       ar->h_stage = nullptr;
       ar->h_stage_bytes = 0;
-      const size_t want = std::max<size_t>(total * 2, 1 << 16);
+      const size_t want = std::max<size_t>(pb.bytes * 2, 1 << 16);
       e = cudaHostAlloc(&ar->h_stage, want, cudaHostAllocDefault);
       if (e != cudaSuccess) return e;
       ar->h_stage_bytes = want;
     }
-    uint8_t* h = static_cast<uint8_t*>(ar->h_stage);
-    memcpy(h, pb.hs.blob.data(), pb.hs.bytes);
-    memcpy(h + pb.off_red, pb.red.data(), pb.red.size() * sizeof(ReduceDesc));
-    return cudaMemcpyAsync(ar->d_buf, h, total, cudaMemcpyHostToDevice, st);
+    pack_plan(pb, static_cast<uint8_t*>(ar->h_stage));
+    return cudaMemcpyAsync(ar->d_buf, ar->h_stage, pb.bytes, cudaMemcpyHostToDevice, st);
   }
-  e = cudaMemcpyAsync(ar->d_buf, pb.hs.blob.data(), pb.hs.bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(static_cast<uint8_t*>(ar->d_buf) + pb.off_red, pb.red.data(),
-                        pb.red.size() * sizeof(ReduceDesc), cudaMemcpyHostToDevice, st);
+  std::vector<uint8_t> img(pb.bytes);
+  pack_plan(pb, img.data());
+  e = cudaMemcpyAsync(ar->d_buf, img.data(), pb.bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
 }
 
-// The persistent sketch launch and the batched reduce of an uploaded plan
-// (the caller counts them).
+// The split pass (if any member needs it), the persistent sketch launch and
+// the batched reduce of an uploaded plan.  Counts the split and sketch
+// launches (the reduce counts itself).
 cudaError_t launch_plan(const PlannedBatch& pb, const BatchArena& ar, cudaStream_t st) {
+  uint8_t* b = static_cast<uint8_t*>(ar.d_buf);
+  if (!pb.splits.empty()) {
+    const int64_t blocks = std::min<int64_t>((pb.prefix.back() + 255) / 256,
+                                             static_cast<int64_t>(num_sms_tc()) * 16);
+    k_split_bf16x2_many<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, st>>>(
+        reinterpret_cast<const SplitDesc*>(b + pb.off_split),
+        reinterpret_cast<const int64_t*>(b + pb.off_prefix), static_cast<int>(pb.splits.size()));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+  }
   const LeftSched sc = device_sched(pb.hs, ar.d_buf, ar.d_status);
   const cudaError_t e = launch_left<kMixed, true>(sc, pb.units, st);
   if (e != cudaSuccess) return e;
-  return splitk_reduce_batched(
-      reinterpret_cast<const ReduceDesc*>(static_cast<uint8_t*>(ar.d_buf) + pb.off_red),
-      static_cast<int>(pb.red.size()), pb.max_elems, st);
+  count_launches(1);
+  return splitk_reduce_batched(reinterpret_cast<const ReduceDesc*>(b + pb.off_red),
+                               static_cast<int>(pb.red.size()), pb.max_elems, st);
 }
 
 int64_t spread_item_stages(const BatchMember& mb) {
@@ -1449,16 +1640,16 @@ int64_t spread_item_stages(const BatchMember& mb) {
   const LeftPlan pl = left_geometry(s, true);
   const int64_t units = std::max<int64_t>(1, pair_slots() / 2);
   const int64_t tiles = pl.tiles_p * pl.tiles_q;
-  const int64_t steps_total = (s.L + BK - 1) / BK;
+  const int64_t rows16 = (s.L + 15) / 16;  // in 16-row units, like every item length
   int64_t splits = (units + tiles - 1) / tiles;
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, steps_total / 64));
-  return (steps_total + splits - 1) / splits;
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, rows16 / 64));
+  return (rows16 + splits - 1) / splits;
 }
 
 size_t batch_member_workspace(const BatchMember& mb, int64_t item_stages) {
   GemmShape s;
   const LeftPlan pl = member_plan(mb, item_stages, &s);
-  return ((static_cast<size_t>(pl.splits) * s.P * s.Q + 63) / 64 * 64) * sizeof(float);
+  return split_bytes(s.L, s.Q) + partial_bytes(pl, s);
 }
 
 cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t item_stages,
@@ -1469,7 +1660,6 @@ cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t i
   if (e == cudaSuccess) e = upload_plan(pb, ar, st);
   if (e == cudaSuccess && ready) e = cudaStreamWaitEvent(st, ready, 0);
   if (e == cudaSuccess) e = launch_plan(pb, *ar, st);
-  if (e == cudaSuccess) count_launches(1);  // the reduce counted itself
   return e;
 }
 
@@ -1575,9 +1765,7 @@ cudaError_t batch_launch(sk_batch* b, cudaStream_t st) {
 sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
   // the legacy default stream cannot be captured: launch directly there
   if (!use_graph || st == nullptr) {
-    const cudaError_t e = batch_launch(b, st);
-    if (e == cudaSuccess) sk::count_launches(1);  // the reduce counted itself
-    return to_status(e);
+    return to_status(batch_launch(b, st));  // launch_plan counted its kernels
   }
   if (b->graph == nullptr) {
     cudaGraph_t g = nullptr;
@@ -1597,7 +1785,7 @@ sk_status batch_run_once(sk_batch* b, cudaStream_t st, bool use_graph) {
     }
   }
   const cudaError_t e = cudaGraphLaunch(b->graph, st);
-  if (e == cudaSuccess) sk::count_launches(2);  // the sketch and the reduce kernels
+  if (e == cudaSuccess) sk::count_launches(b->plan.launches);  // split, sketch, reduce
   return to_status(e);
 }
 
@@ -1635,7 +1823,7 @@ sk_status sk_batch_add(sk_batch_handle b, sk_handle h, const float* A, int64_t m
   s.L = m;
   const sk_status st = sk::tc_check(s, A, lda, Y, ldy);
   if (st != SK_OK) return st;
-  sk::BatchMember e{h->seed, h->dist, h->k, h->scale, A, m, n, lda, Y, ldy, nullptr, 0};
+  sk::BatchMember e{h->seed, h->dist, h->k, h->scale, A, m, n, lda, Y, ldy, nullptr, 0, false};
   b->entries.push_back(e);
   batch_invalidate(b);
   return SK_OK;
