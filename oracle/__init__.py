@@ -72,6 +72,11 @@ def lib():
             L.orc_e4m3_rne.restype = None
             L.orc_e4m3_value.argtypes = [vp, vp, i64]
             L.orc_e4m3_value.restype = None
+            L.orc_quantize_rows_e4m3.argtypes = [vp, i64, i64, i64, vp, i64, vp]
+            L.orc_quantize_rows_e4m3.restype = ctypes.c_int
+            L.orc_apply_right_q8.argtypes = [u64, i32, i64, vp, vp, i64, i64, i64, vp, i64, vp,
+                                             i64, i32]
+            L.orc_apply_right_q8.restype = ctypes.c_int
             L.orc_scale.argtypes = [i64]
             L.orc_scale.restype = ctypes.c_float
             L.orc_generate.argtypes = [u64, i32, i32, u32, i64, i64, i64, i64, vp, i64]
@@ -193,4 +198,38 @@ def apply_right(seed: int, dist: int, prec: int, k: int, A: np.ndarray, rows=Non
                                int(nthreads or os.cpu_count() or 1))
     if rc != 0:
         raise ValueError("orc_apply_right failed")
+    return Y
+
+
+def quantize_rows_e4m3(A: np.ndarray):
+    """(codes, exps): E4M3 codes of A[m x n] with one power-of-two scale 2^exps[i]
+    per row, the smallest with max_j |a_ij| <= 448 * 2^exps[i] (0 for a zero
+    row); codes[i, j] = RNE_e4m3(a_ij * 2^-exps[i])."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    m, n = A.shape
+    codes = np.empty((m, n), dtype=np.uint8)
+    exps = np.empty(m, dtype=np.int32)
+    if lib().orc_quantize_rows_e4m3(_p(A), m, n, n, _p(codes), n, _p(exps)) != 0:
+        raise ValueError("orc_quantize_rows_e4m3 failed")
+    return codes, exps
+
+
+def apply_right_q8(seed: int, dist: int, k: int, codes: np.ndarray, exps: np.ndarray, rows=None,
+                   nthreads: int | None = None) -> np.ndarray:
+    """FP8 right sketch in FP64: Y[i, j] = 2^exps[i] s sum_c value(codes[i, c])
+    value(RNE_e4m3(g(j, c))) (optionally only the rows ``rows``)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    exps = np.ascontiguousarray(exps, dtype=np.int32)
+    m, n = codes.shape
+    if rows is None:
+        idx, nidx = None, m
+    else:
+        idx = np.ascontiguousarray(rows, dtype=np.int64)
+        nidx = idx.size
+    Y = np.empty((nidx, k), dtype=np.float64)
+    rc = lib().orc_apply_right_q8(int(seed), int(dist), int(k), _p(codes), _p(exps), m, n, n,
+                                  None if idx is None else _p(idx), nidx, _p(Y), k,
+                                  int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("orc_apply_right_q8 failed")
     return Y

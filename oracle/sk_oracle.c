@@ -327,6 +327,7 @@ int orc_generate(uint64_t seed, int dist, int prec, uint32_t dom, int64_t row0, 
 typedef struct {
   uint64_t seed; int dist, prec; int64_t k;
   const float* A; int64_t m, n, lda;
+  const uint8_t* Aq; const int32_t* exps;  /* FP8 right sketch: codes of A, row exponents */
   const int64_t* idx; int64_t nidx;   /* output column (left) / row (right) subset */
   double* Y; int64_t ldy;
   const double* S;                    /* right sketch: full S, k x n, scaled */
@@ -463,6 +464,84 @@ int orc_apply_right(uint64_t seed, int dist, int prec, int64_t k, const float* A
   J.A = A; J.m = m; J.n = n; J.lda = lda; J.idx = idx; J.nidx = nidx; J.Y = Y; J.ldy = ldy;
   J.S = S;
   int rc = run_jobs(&J, nidx, nthreads, right_worker);
+  free(S);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP8 (E4M3) form of A                                                      */
+/* ------------------------------------------------------------------------ */
+/* The paper is silent on low precision; this library's reading of "E4M3 A
+ * with per-tile scales" (the tile being one row of A, which spans the whole
+ * contracted dimension of the right sketch, so the scale factors out of every
+ * dot product):
+ *   e_i  = the smallest integer with max_j |a_ij| <= 448 * 2^e_i (0 for a row
+ *          of zeros),
+ *   A_q(i, j) = RNE_e4m3(a_ij * 2^-e_i).
+ * Scaling by a power of two is exact, so each code is the E4M3 rounding of a
+ * known number; no code saturates (|a_ij| 2^-e_i <= 448, E4M3's largest). */
+int orc_quantize_rows_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, uint8_t* Aq,
+                           int64_t ldq, int32_t* exps) {
+  if (m <= 0 || n <= 0 || lda < n || ldq < n) return -1;
+  for (int64_t i = 0; i < m; ++i) {
+    const float* a = A + i * lda;
+    double amax = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      const double v = fabs((double)a[j]);
+      if (v > amax) amax = v;
+    }
+    int e = 0;
+    if (amax > 0.0) {
+      e = ilogb(amax) - 8;
+      while (ldexp(amax, -e) > 448.0) ++e;
+      while (ldexp(amax, -(e - 1)) <= 448.0) --e;
+    }
+    exps[i] = e;
+    for (int64_t j = 0; j < n; ++j) Aq[i * ldq + j] = e4m3_rne((float)ldexp((double)a[j], -e));
+  }
+  return 0;
+}
+
+/* FP8 right sketch: Y[ii][j] = 2^{e_i} s sum_c value(A_q(i, c)) value(RNE_e4m3(g(j, c)))
+ * for the rows i = idx[ii] (idx NULL: all m rows). */
+static void* right_q8_worker(void* arg) {
+  job_t* J = (job_t*)arg;
+  double* arow = (double*)malloc(sizeof(double) * (size_t)J->n);
+  if (!arow) { J->status = -1; return NULL; }
+  for (int64_t ii = J->i_begin; ii < J->i_end; ++ii) {
+    int64_t i = J->idx ? J->idx[ii] : ii;
+    const uint8_t* q = J->Aq + i * J->lda;
+    for (int64_t c = 0; c < J->n; ++c) arow[c] = e4m3_value(q[c]);
+    const double rs = ldexp(1.0, J->exps[i]);
+    for (int64_t j = 0; j < J->k; ++j) {
+      const double* srow = J->S + j * J->n;
+      double acc = 0.0;
+      for (int64_t c = 0; c < J->n; ++c) acc += arow[c] * srow[c];
+      J->Y[ii * J->ldy + j] = rs * acc;
+    }
+  }
+  free(arow);
+  J->status = 0;
+  return NULL;
+}
+
+int orc_apply_right_q8(uint64_t seed, int dist, int64_t k, const uint8_t* Aq,
+                       const int32_t* exps, int64_t m, int64_t n, int64_t ldq,
+                       const int64_t* idx, int64_t nidx, double* Y, int64_t ldy, int nthreads) {
+  if (k <= 0 || m <= 0 || n <= 0 || ldq < n || nidx < 0 || ldy < k) return -1;
+  if (!idx && nidx != m) return -1;
+  double* S = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  if (!S) return -1;
+  const double s = (double)orc_scale(k);
+  for (int64_t j = 0; j < k; ++j) {
+    gen_row(seed, dist, ORC_E4M3, 0u, (uint32_t)j, 0, n, S + j * n);
+    for (int64_t c = 0; c < n; ++c) S[j * n + c] *= s;
+  }
+  job_t J = {0};
+  J.seed = seed; J.dist = dist; J.prec = ORC_E4M3; J.k = k;
+  J.Aq = Aq; J.exps = exps; J.m = m; J.n = n; J.lda = ldq; J.idx = idx; J.nidx = nidx;
+  J.Y = Y; J.ldy = ldy; J.S = S;
+  int rc = run_jobs(&J, nidx, nthreads, right_q8_worker);
   free(S);
   return rc;
 }

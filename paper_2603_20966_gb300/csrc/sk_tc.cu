@@ -80,6 +80,11 @@ constexpr int WARP_WORK0 = WARP_EPI0 + NUM_EPI_WARPS;
 constexpr int NWORK = 32 * NUM_WORK_WARPS;
 constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 
+// Epilogue transpose tile of one warp: 32 accumulator rows x 16 columns,
+// rows padded to 20 floats (16-byte aligned, few bank conflicts).
+constexpr int EPI_PITCH = 20;
+constexpr uint32_t EPI_TILE = 32 * EPI_PITCH * 4;
+
 // Per-CTA buffers of the left kernel.  A CTA of a pair holds NT/2 columns of
 // each split A tile.
 template <bool PAIR>
@@ -92,12 +97,13 @@ struct Cfg {
   static constexpr int NGROUPS = PAIR ? 4 : 2;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NSO = PAIR ? 5 : 3;                  // operand stages
+  static constexpr int NSO = PAIR ? 5 : 2;                  // operand stages
   static constexpr uint32_t OPB = 2u * COLS * LK * 2u;      // hi and lo tiles of a stage
   static constexpr uint32_t OPS = BM * LK * 2;              // S tile: KSTEPS slabs of 16
   static constexpr uint32_t OFF_B = 0;
   static constexpr uint32_t OFF_S = OFF_B + NSO * OPB;
-  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
+  static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;    // epilogue transpose tiles
+  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
   static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
@@ -258,8 +264,11 @@ __global__ void __launch_bounds__(256)
 // Per-item geometry shared by every role.
 struct ItemGeo {
   const LeftProblem* pr;
+  int64_t P;      // rows of S (copied: the workers' loop keeps it in a register)
+  PhiloxKey key;  // (likewise)
   int64_t p0, q0, lbeg, lend;
   int nsteps, nt, nmma, nh, bh, cols, dist;
+  int coff;  // stages by which this item's chain boundaries are shifted
 };
 
 template <bool PAIR>
@@ -267,6 +276,8 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
   const LeftItem it = sc.items[idx];
   ItemGeo g;
   g.pr = sc.probs + it.prob;
+  g.P = g.pr->P;
+  g.key = g.pr->key;
   g.nt = g.pr->nt;
   g.dist = g.pr->dist;
   g.nmma = g.nt > 256 ? 2 : 1;
@@ -278,6 +289,11 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
   g.lbeg = static_cast<int64_t>(it.z) * g.pr->chunk;
   g.lend = min(g.pr->L, g.lbeg + g.pr->chunk);
   g.nsteps = static_cast<int>((g.lend - g.lbeg + LK - 1) / LK);
+  // Items of one problem shift their chain boundaries by different amounts so
+  // that the accumulator drains of concurrent pairs do not all reach L2 at
+  // once; the shift is a function of the item alone, so the summation order
+  // of a problem does not depend on what runs beside it.
+  g.coff = ((it.tp * 7 + it.z * 13 + it.tq * 5) & 7) * (CHAIN_L / 8);
   return g;
 }
 
@@ -297,11 +313,11 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
       const uint32_t r = static_cast<uint32_t>(t);
       const int64_t grow = g.p0 + r;
       uint32_t bits = 0u, valid = 0u;
-      if (grow < g.pr->P && cbase < g.lend) {
+      if (grow < g.P && cbase < g.lend) {
         const uint32_t c = static_cast<uint32_t>(cbase);  // a multiple of 32
         const uint32_t blk = c >> 7;
         if (blk != cached_blk[it]) {
-          words[it] = rademacher_bits(g.pr->key, static_cast<uint32_t>(grow), blk, 0u);
+          words[it] = rademacher_bits(g.key, static_cast<uint32_t>(grow), blk, 0u);
           cached_blk[it] = blk;
         }
         const uint32_t wsel = (c >> 5) & 3u;
@@ -347,11 +363,11 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
       const int64_t grow = g.p0 + r;
       const int64_t c0 = cbase + 16 * slab + 4 * qd;
       uint2 v = make_uint2(0u, 0u);
-      if (grow < g.pr->P && c0 < g.lend) {
+      if (grow < g.P && c0 < g.lend) {
         const uint32_t c = static_cast<uint32_t>(c0);
         const float4 a = DIST == kUniform
-                             ? uniform4(g.pr->key, static_cast<uint32_t>(grow), c >> 2, 0u)
-                             : gaussian4(g.pr->key, static_cast<uint32_t>(grow), c >> 2, 0u);
+                             ? uniform4(g.key, static_cast<uint32_t>(grow), c >> 2, 0u)
+                             : gaussian4(g.key, static_cast<uint32_t>(grow), c >> 2, 0u);
         v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
       }
       *reinterpret_cast<uint2*>(sdst + slab * S_SLAB + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
@@ -463,9 +479,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * HCHUNK_BYTES;
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
-          const int in_chain = s % CHAIN_L;
+          const int ph = (s + ig.coff) % CHAIN_L;
+          const bool chain_start = s == 0 || ph == 0;
           // a new chain may start only after every epilogue has read the last one
-          if (in_chain == 0 && gc > 0 && !mbar_wait(acc_empty, (gc - 1) & 1, ab, 0x25, gc)) {
+          if (chain_start && gc > 0 && !mbar_wait(acc_empty, (gc - 1) & 1, ab, 0x25, gc)) {
             stop = true;
             break;
           }
@@ -486,7 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     bslot + static_cast<uint32_t>(pass) * pstride +
                         static_cast<uint32_t>(h) * hstride + ks * B_KSTEP,
                     B_LBO, B_SBO);
-                const uint32_t acc = (in_chain > 0 || ks > 0 || pass > 0) ? 1u : 0u;
+                const uint32_t acc = (!chain_start || ks > 0 || pass > 0) ? 1u : 0u;
                 if (PAIR)
                   mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
                 else
@@ -494,7 +511,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             }
           }
-          const bool chain_end = in_chain == CHAIN_L - 1 || s == ig.nsteps - 1;
+          const bool chain_end = ph == CHAIN_L - 1 || s == ig.nsteps - 1;
           if (PAIR) {  // operands and accumulator are both CTAs'
             mma_commit_pair_both(empty_o(so));
             if (chain_end) mma_commit_pair_both(acc_full);
@@ -514,19 +531,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp < WARP_WORK0) {
     // ---- epilogue: add each finished chain into the item's FP32 partial ----
+    // A warp reads 32 accumulator rows (its TMEM lane quarter) x 32 columns,
+    // then writes them through a transpose tile so that every global store /
+    // reduction instruction covers 64-byte pieces of 8 rows instead of 16
+    // bytes of 32 rows.
     const int quarter = warp & 3;
     const int colset = (warp - WARP_EPI0) >> 2;  // 0 or 1: even / odd 32-column chunks
-    const int row = quarter * 32 + lane;
+    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * EPI_TILE);
+    const int rsub = lane >> 2;       // row within a group of 8 (read side)
+    const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
     int gc = 0;
     bool stop = false;
     for (int idx = ib; idx < ie && !stop; ++idx) {
       const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
       const LeftItem it = sc.items[idx];
-      const int64_t gp = ig.p0 + row;
       const int64_t P = ig.pr->P, Q = ig.pr->Q;
-      float* dst_row = ig.pr->part + (static_cast<int64_t>(it.z) * P + gp) * Q + ig.q0;
+      float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * Q + ig.q0;
       const bool vec_ok = (Q % 4) == 0;
-      const int nchains = (ig.nsteps + CHAIN_L - 1) / CHAIN_L;
+      const int nchains = (ig.nsteps + ig.coff + CHAIN_L - 1) / CHAIN_L;
       for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
         const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
         if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
@@ -543,36 +565,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         static_cast<uint32_t>(ci * 32),
                     v);
           tmem_ld_wait();
-          if (gp < P) {
 #pragma unroll
-            for (int e = 0; e < 32; e += 4) {  // bh is a multiple of 8: groups never straddle
-              const int tcol = ci * 32 + e;
-              const int h = tcol >> 8;
-              const int c = tcol & 255;
-              if (c >= ig.nh) continue;
-              const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
-                                  : tcol;
-              const int64_t col = ig.q0 + tn;
-              float* d = dst_row + tn;
-              const float a0 = __uint_as_float(v[e]), a1 = __uint_as_float(v[e + 1]);
-              const float a2 = __uint_as_float(v[e + 2]), a3 = __uint_as_float(v[e + 3]);
-              if (vec_ok && col + 4 <= Q) {
-                if (c0 == 0)
-                  *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
-                else
-                  red_add_v4(d, a0, a1, a2, a3);
-              } else {
-                const float vv[4] = {a0, a1, a2, a3};
-                for (int u = 0; u < 4; ++u) {
-                  if (col + u < Q) {
-                    if (c0 == 0)
-                      d[u] = vv[u];
-                    else
-                      red_add(d + u, vv[u]);
+          for (int half = 0; half < 2; ++half) {
+            // lane = accumulator row: its 16 columns into the tile
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
+                  make_float4(__uint_as_float(v[16 * half + 4 * q]),
+                              __uint_as_float(v[16 * half + 4 * q + 1]),
+                              __uint_as_float(v[16 * half + 4 * q + 2]),
+                              __uint_as_float(v[16 * half + 4 * q + 3]));
+            __syncwarp();
+            // 4 consecutive columns (bh is a multiple of 8: they never straddle)
+            const int tcol = ci * 32 + 16 * half + csub;
+            const int h = tcol >> 8;
+            const int c = tcol & 255;
+            const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
+                                : tcol;
+            const int64_t col = ig.q0 + tn;
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass) {
+              const int rr = 8 * pass + rsub;
+              const int64_t gp = ig.p0 + quarter * 32 + rr;
+              const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
+              if (c < ig.nh && gp < P) {
+                float* d = part_item + gp * Q + tn;
+                if (vec_ok && col + 4 <= Q) {
+                  if (c0 == 0)
+                    *reinterpret_cast<float4*>(d) = a;
+                  else
+                    red_add_v4(d, a.x, a.y, a.z, a.w);
+                } else {
+                  const float vv[4] = {a.x, a.y, a.z, a.w};
+                  for (int u = 0; u < 4; ++u) {
+                    if (col + u < Q) {
+                      if (c0 == 0)
+                        d[u] = vv[u];
+                      else
+                        red_add(d + u, vv[u]);
+                    }
                   }
                 }
               }
             }
+            __syncwarp();
           }
         }
         tc_fence_before();
