@@ -484,7 +484,9 @@ def run_ours(args):
     if world > 1:
         tdist.init_process_group("nccl", device_id=dev)
     m, n, k, dists, side = WORKLOADS[args.workload]
-    form = {"fp32": P.SK_FP32, "bf16x2": P.SK_BF16X2}[args.form]
+    form = {"fp32": P.SK_FP32, "bf16x2": P.SK_BF16X2, "fp8": P.SK_FP8E4M3}[args.form]
+    if form == P.SK_FP8E4M3 and side != "right":
+        raise SystemExit("the FP8 form is the right sketch only (workload C3)")
     stream = torch.cuda.current_stream(dev)
     apply = P.sk_apply_left if side == "left" else P.sk_apply_right
     apply_host = P.sk_apply_left_host if side == "left" else P.sk_apply_right_host
@@ -563,6 +565,15 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": flops_per_sketch / avg_kernel_s / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x "
                                                 "max SM clock"}
+    elif side == "right" and form == P.SK_FP8E4M3:
+        # the timed kernel is the FP8 sketch: E4M3 A read once, Y written once
+        algo_bytes = 1.0 * m * n + 4.0 * m * k
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": algo_bytes / avg_kernel_s / 1e9, "peak": peak,
+                "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth",
+                "note": "timed kernel = the FP8 sketch; achieved = (E4M3 A bytes + Y bytes) / "
+                        "its time; the step also runs the row quantizer (FP32 A read once, "
+                        "codes written once)"}
     elif side == "right":
         # HBM-bound: A read once, Y written once
         algo_bytes = 4.0 * m * n + 4.0 * m * k
@@ -580,6 +591,32 @@ def run_ours(args):
     roof["traffic"] = measured_traffic() if (form != P.SK_FP32 and args.workload == "C2") else None
     roof["kernel_ms_by_dist"] = {DIST_NAME[d]: statistics.mean(kernel_ms[j::len(dists)])
                                  for j, d in enumerate(dists)}
+
+    fp8 = None
+    if form == P.SK_FP8E4M3:
+        # a resident quantized A (quantized once, outside the timed region)
+        ldq = (n + 15) // 16 * 16
+        Aq = torch.empty((m, ldq), dtype=torch.uint8, device=dev)
+        ex = torch.empty((m,), dtype=torch.int32, device=dev)
+        P.sk_quantize_e4m3(A, m, n, n, Aq, ldq, ex, stream)
+        for _ in range(2):
+            for d in dists:
+                P.sk_apply_right_e4m3(hs[d], Aq, ex, m, n, ldq, Ys[d], yshape[1], stream)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            for d in dists:
+                P.sk_apply_right_e4m3(hs[d], Aq, ex, m, n, ldq, Ys[d], yshape[1], stream)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        qms = q0.elapsed_time(q1) / args.steps
+        fp8 = {"resident_e4m3_a": {"ms_per_step": qms,
+                                   "tflops": flops_step / (qms * 1e-3) / 1e12,
+                                   "hbm_gbs": len(dists) * (m * n + 4.0 * m * k) / (qms * 1e-3) / 1e9},
+               "note": "resident: A quantized once (sk_quantize_e4m3) and sketched by "
+                       "sk_apply_right_e4m3 each step; error vs the exact product is reported "
+                       "by tests/test_gpu_fp8.py (about 3-4 %)"}
+        del Aq, ex
 
     # end to end through the host-buffer entry points
     e2e = None
@@ -631,7 +668,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16x2": "bf16x2"}[args.form], "data": "synthetic",
+            "dtype": {"fp32": "f32", "bf16x2": "bf16x2", "fp8": "e4m3"}[args.form],
+            "data": "synthetic",
             "config": {"workload": f"{args.workload} {side} sketch A {m}x{n} FP32 "
                                    f"{'U V^T + 1e-3 E' if args.workload == 'C3' else 'N(0,1)'}, "
                                    f"k={k}, S {[DIST_NAME[d] for d in dists]} Philox4x32-10 "
@@ -642,6 +680,8 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
             "cpu_baseline": cpu,
         }
+        if fp8 is not None:
+            line["fp8"] = fp8
         print(json.dumps(line), flush=True)
     if world > 1:
         tdist.destroy_process_group()
@@ -654,7 +694,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16x2", choices=["fp32", "bf16x2"])
+    ap.add_argument("--form", default="bf16x2", choices=["fp32", "bf16x2", "fp8"])
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

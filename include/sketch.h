@@ -73,9 +73,13 @@ typedef enum { SK_GAUSSIAN = 0, SK_RADEMACHER = 1, SK_UNIFORM = 2 } sk_dist;
  *  SK_BF16X2   generated operand rounded to BF16, A split into BF16 hi + lo
  *              parts (hi = bf16(a), lo = bf16(a - hi)), two tensor-core MMAs
  *              per tile with FP32 accumulation in tensor memory.
- *  SK_FP8E4M3  generated operand rounded to E4M3, A quantised to E4M3 with
- *              one power-of-two scale per 32 consecutive elements along the
- *              contracted dimension (block-scaled tensor-core MMA).
+ *  SK_FP8E4M3  right sketch only: generated operand rounded to E4M3, A
+ *              quantised to E4M3 with one power-of-two scale per row
+ *              (sk_quantize_e4m3), one kind::f8f6f4 tensor-core MMA per
+ *              tile with FP32 accumulation; the row scale is applied in the
+ *              epilogue.  Low precision is not in the paper; the error
+ *              against the exact product is a few percent (3-bit
+ *              significands), reported rather than held to 1e-5.
  * The 1/sqrt(k) scale is one FP32 multiply in every form's epilogue. */
 typedef enum { SK_FP32 = 0, SK_BF16X2 = 1, SK_FP8E4M3 = 2 } sk_precision;
 
@@ -106,9 +110,30 @@ sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64
                         int64_t ldy, void* stream);
 
 /* Right sketch Y[m x k] = A[m x n] S^T (S: k x n, S(r, c) for r < k,
- * c < n).  Same conventions as sk_apply_left; requires n < 2^32. */
+ * c < n).  Same conventions as sk_apply_left; requires n < 2^32.  In the
+ * SK_FP8E4M3 form the call quantises A into the workspace first
+ * (sk_quantize_e4m3) and then runs sk_apply_right_e4m3 (the left sketch
+ * returns SK_EUNSUPPORTED in that form). */
 sk_status sk_apply_right(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
                          float* Y, int64_t ldy, void* stream);
+
+/* E4M3 form of A for the FP8 right sketch: row_exp[i] = the smallest integer
+ * e with max_j |A[i][j]| <= 448 * 2^e (0 for a row of zeros), and
+ * Aq[i*ldq + j] = RNE_e4m3(A[i][j] * 2^-e) for j < n (OCP E4M3, largest 448,
+ * no code saturates), 0 for n <= j < ldq.  A: device FP32, leading dim
+ * lda >= n; Aq: device, 16-byte aligned, ldq >= n a multiple of 16; row_exp:
+ * device int32[m].  Asynchronous on `stream`.  Errors: SK_EINVAL, SK_ECUDA. */
+sk_status sk_quantize_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, uint8_t* Aq,
+                           int64_t ldq, int32_t* row_exp, void* stream);
+
+/* FP8 right sketch of an already quantised A (as sk_quantize_e4m3 writes it,
+ * e.g. a resident copy reused by many sketches): Y[m x k] =
+ * s 2^row_exp[i] sum_c e4m3(Aq[i][c]) e4m3(g(j, c)), accumulated in FP32 on
+ * the tensor cores.  The handle supplies seed, dist and k whatever its form.
+ * Y: device FP32, 16-byte aligned, ldy >= k a multiple of 4.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+sk_status sk_apply_right_e4m3(sk_handle h, const uint8_t* Aq, const int32_t* row_exp, int64_t m,
+                              int64_t n, int64_t ldq, float* Y, int64_t ldy, void* stream);
 
 /* Left sketch that allocates no device memory, for callers that cannot let
  * a library call cudaMalloc: an application whose device memory belongs to

@@ -491,7 +491,7 @@ int orc_quantize_rows_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, ui
       if (v > amax) amax = v;
     }
     int e = 0;
-    if (amax > 0.0) {
+    if (amax > 0.0 && isfinite(amax)) {  /* a row holding Inf keeps e = 0 */
       e = ilogb(amax) - 8;
       while (ldexp(amax, -e) > 448.0) ++e;
       while (ldexp(amax, -(e - 1)) <= 448.0) --e;

@@ -45,6 +45,8 @@ PROTOTYPES = {
     "sk_batch_status": (_int, [_vp, _vp]),
     "sk_batch_size": (_int, [_vp, _P(_i64)]),
     "sk_batch_destroy": (_int, [_vp]),
+    "sk_quantize_e4m3": (_int, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "sk_apply_right_e4m3": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_server_create": (_int, [_u64, ctypes.c_int32, _P(_vp)]),
     "sk_server_submit": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _P(_i64)]),
     "sk_server_poll": (_int, [_vp, _i64, _P(ctypes.c_double)]),
@@ -329,3 +331,14 @@ def sk_server_reset_stats(s) -> None:
 
 def sk_server_destroy(s) -> None:
     _check("sk_server_destroy", _lib.sk_server_destroy(s))
+
+
+def sk_quantize_e4m3(A, m, n, lda, Aq, ldq, row_exp, stream=None) -> None:
+    _check("sk_quantize_e4m3", _lib.sk_quantize_e4m3(_ptr(A), int(m), int(n), int(lda), _ptr(Aq),
+                                                     int(ldq), _ptr(row_exp), _stream(stream)))
+
+
+def sk_apply_right_e4m3(h, Aq, row_exp, m, n, ldq, Y, ldy, stream=None) -> None:
+    _check("sk_apply_right_e4m3", _lib.sk_apply_right_e4m3(h, _ptr(Aq), _ptr(row_exp), int(m),
+                                                           int(n), int(ldq), _ptr(Y), int(ldy),
+                                                           _stream(stream)))

@@ -39,6 +39,7 @@ bool valid_prec(int p) { return p == SK_FP32 || p == SK_BF16X2 || p == SK_FP8E4M
 
 size_t workspace_for(const sk_sketch* h, const GemmShape& s) {
   if (h->prec == SK_FP32) return sk::simt_workspace_bytes(s);
+  if (h->prec == SK_FP8E4M3) return s.left ? 0 : sk::q8_workspace_bytes(s);
   return sk::tc_workspace_bytes(s);
 }
 
@@ -84,16 +85,21 @@ sk_status apply(sk_sketch* h, const float* A, int64_t m, int64_t n, int64_t lda,
   } else {
     s.P = m; s.Q = h->k; s.L = n;
   }
-  if (h->prec != SK_FP32) {
+  if (h->prec == SK_FP8E4M3 && left) return SK_EUNSUPPORTED;  // FP8: right sketch only
+  if (h->prec == SK_BF16X2) {
     st = sk::tc_check(s, A, lda, Y, ldy);
     if (st != SK_OK) return st;
   }
+  if (h->prec == SK_FP8E4M3 && ((reinterpret_cast<uintptr_t>(Y) & 15u) || ldy % 4 != 0))
+    return SK_EINVAL;
   st = ensure_workspace(h, workspace_for(h, s));
   if (st != SK_OK) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (h->prec == SK_FP32)
     e = sk::simt_sketch(h, s, A, lda, Y, ldy, h->ws, h->ws_bytes, cs);
+  else if (h->prec == SK_FP8E4M3)
+    e = sk::q8_sketch_right(h, s, A, lda, Y, ldy, h->ws, h->ws_bytes, cs);
   else
     e = sk::tc_sketch(h, s, A, lda, Y, ldy, h->ws, h->ws_bytes, cs);
   return from_cuda(e);
@@ -210,6 +216,35 @@ sk_status sk_materialize(sk_handle h, int64_t row0, int64_t col0, int64_t rows, 
   if (row0 + rows > kMaxIndex || col0 + cols > kMaxIndex) return SK_EINVAL;
   return from_cuda(sk::materialize(h, row0, col0, rows, cols, fmt, scaled, out, ld,
                                    static_cast<cudaStream_t>(stream)));
+}
+
+sk_status sk_quantize_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, uint8_t* Aq,
+                           int64_t ldq, int32_t* row_exp, void* stream) {
+  if (!A || !Aq || !row_exp || m <= 0 || n <= 0 || lda < n || ldq < n || ldq % 16 != 0)
+    return SK_EINVAL;
+  if (reinterpret_cast<uintptr_t>(Aq) & 15u) return SK_EINVAL;
+  return from_cuda(sk::q8_quantize(A, lda, m, n, Aq, ldq, row_exp,
+                                   static_cast<cudaStream_t>(stream)));
+}
+
+sk_status sk_apply_right_e4m3(sk_handle h, const uint8_t* Aq, const int32_t* row_exp, int64_t m,
+                              int64_t n, int64_t ldq, float* Y, int64_t ldy, void* stream) {
+  if (!h || !Aq || !row_exp || !Y || m <= 0 || n <= 0 || ldq < n || ldq % 16 != 0 ||
+      ldy < h->k)
+    return SK_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(Aq) & 15u) || (reinterpret_cast<uintptr_t>(Y) & 15u) ||
+      ldy % 4 != 0)
+    return SK_EINVAL;
+  if (n >= kMaxIndex || m >= (1LL << 31)) return SK_EINVAL;
+  GemmShape s;
+  s.left = false;
+  s.P = m;
+  s.Q = h->k;
+  s.L = n;
+  const sk_status st = ensure_workspace(h, sk::q8_partial_bytes(s));
+  if (st != SK_OK) return st;
+  return from_cuda(sk::q8_sketch_right_quantized(h, s, Aq, row_exp, ldq, Y, ldy, h->ws,
+                                                 h->ws_bytes, static_cast<cudaStream_t>(stream)));
 }
 
 sk_status sk_workspace_size(sk_handle h, int side, int64_t m, int64_t n, size_t* bytes) {

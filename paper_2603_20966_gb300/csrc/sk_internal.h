@@ -127,4 +127,17 @@ sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float*
 cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                       float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
 
+// ---- FP8 (E4M3) form of the right sketch (sk_tc.cu) ----
+int64_t q8_ld(int64_t n);  // row stride (bytes) of the codes of an n-column A
+cudaError_t q8_quantize(const float* A, int64_t lda, int64_t m, int64_t n, uint8_t* Aq,
+                        int64_t ldq, int32_t* exps, cudaStream_t st);
+size_t q8_partial_bytes(const GemmShape& s);
+// codes + row exponents + partials of an apply call that quantizes A itself
+size_t q8_workspace_bytes(const GemmShape& s);
+cudaError_t q8_sketch_right_quantized(const sk_sketch* h, const GemmShape& s, const uint8_t* Aq,
+                                      const int32_t* exps, int64_t ldq, float* Y, int64_t ldy,
+                                      void* part, size_t part_bytes, cudaStream_t st);
+cudaError_t q8_sketch_right(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                            float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
+
 }  // namespace sk

@@ -42,6 +42,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <stdio.h>
@@ -1007,6 +1008,419 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// FP8 form of the right sketch: Y[m x k] = s diag(2^e) A_q S_q^T, A_q the E4M3
+// codes of A with one power-of-two scale 2^e_i per row, S_q = E4M3(g).
+//
+// Stages of 128 columns of n.  TMA brings this CTA's 256 rows of A_q (rows of
+// 128 B, 128-byte swizzle); the workers generate this CTA's half of the E4M3
+// S tile (K-major, no swizzle); per stage the even CTA issues 4 K steps x 2
+// accumulators of tcgen05.mma kind::f8f6f4 (M = 256 over the pair, N = nq,
+// K = 32).  The epilogue multiplies each row by its 2^e (exact) before adding
+// the chain into the partial.  Roles, chains and bounded waits are those of
+// the BF16 right kernel.
+// ---------------------------------------------------------------------------
+constexpr int QK = 128;     // contracted columns (bytes of A_q) per FP8 stage
+constexpr int QCHAIN = 32;  // FP8 stages per accumulation chain (128 K steps)
+
+struct CfgQ {
+  static constexpr int ROWS = 256;  // rows of A per CTA (two 128-row accumulators)
+  static constexpr int NGROUPS = 4;
+  static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
+  static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
+  static constexpr int NSO = 4;
+  static constexpr uint32_t OPA = ROWS * QK;  // 32 KB of A_q
+  static constexpr uint32_t OPS = 128 * QK;   // 16 KB: this CTA's half of the S tile
+  static constexpr uint32_t OFF_A = 0;
+  static constexpr uint32_t OFF_S = OFF_A + NSO * OPA;
+  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
+  static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
+  static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(NGROUPS <= NSO, "worker groups vs ring depth");
+};
+
+// E4M3 S tile: [row/8][16-column block][row%8][16 B] -- K-major core matrices
+// with 128 B between column blocks (LBO) and 1024 B between 8-row groups (SBO).
+__device__ __forceinline__ uint32_t q8_off(uint32_t row, uint32_t col) {
+  return (row >> 3) * 1024u + (col >> 4) * 128u + (row & 7u) * 16u + (col & 15u);
+}
+
+// Four consecutive +-1 entries (bits b0..b3 of x, set = -1) as E4M3 bytes:
+// +1 = 0x38, -1 = 0xB8.  The multiply spreads bit i to bit 8i (no carries).
+__device__ __forceinline__ uint32_t rad4_e4m3(uint32_t x) {
+  return (((x & 0xFu) * 0x00204081u) & 0x01010101u) << 7 | 0x38383838u;
+}
+
+__device__ __forceinline__ uint32_t e4m3x4(float4 a) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a.x, a.y), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(a.z, a.w), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+struct TcRightQParams {
+  float* part;          // partials [splits][P][Q]
+  const int32_t* exps;  // row exponents of A_q
+  int64_t P, Q, L;      // P = m, Q = k, L = n
+  int64_t chunk;        // columns per split (multiple of QK)
+  int nq;               // N of the MMA: k rows per pair tile (multiple of 16, <= 256)
+  int tmem_cols;        // power of two >= 2 * nq
+  PhiloxKey key;
+  int* status;
+  uint64_t timeout_ns;
+};
+
+template <int DIST>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_sketch_e4m3_right(const __grid_constant__ CUtensorMap tmapA, const TcRightQParams p) {
+  using C = CfgQ;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar0 = sbase + C::OFF_BAR;
+  auto full_a = [&](int i) { return bar0 + 8u * i; };
+  auto full_o = [&](int i) { return bar0 + 8u * (C::NSO + i); };
+  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (3 * C::NSO);
+  const uint32_t acc_empty = acc_full + 8u;
+  const uint32_t drain_bar = acc_full + 16u;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank() & 1u;  // 0 = even CTA (MMA issuer)
+  const bool leader = rank == 0;
+  const int nq = p.nq;
+  const int gh = nq / 2;                                          // S rows this CTA generates
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * C::ROWS;  // this CTA's rows of A
+  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nq;       // the pair's k rows
+  const int64_t g0 = q0 + static_cast<int64_t>(rank) * gh;        // this CTA's S rows
+  const int64_t lbeg = static_cast<int64_t>(blockIdx.z) * p.chunk;
+  const int64_t lend = min(p.L, lbeg + p.chunk);
+  const int nsteps = static_cast<int>((lend - lbeg + QK - 1) / QK);
+  const int nchains = (nsteps + QCHAIN - 1) / QCHAIN;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NSO; ++i) {
+      mbar_init(full_a(i), 1);
+      mbar_init(full_o(i), C::GROUP_WARPS * 2);
+      mbar_init(empty_o(i), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NUM_EPI_WARPS * 2);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == WARP_MMA) {
+    tmem_alloc_pair(smem_u32(tmem_slot), static_cast<uint32_t>(p.tmem_cols));
+    tmem_relinquish_pair();
+  }
+  if (warp == WARP_TMA && lane == 0) tma_prefetch_desc(&tmapA);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const Abort ab{abort_flag, p.status, p.timeout_ns};
+  const uint32_t lead_full_o = mapa_shared(full_o(0), 0u);
+  const uint32_t lead_acc_empty = mapa_shared(acc_empty, 0u);
+
+  if (warp == WARP_TMA) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nsteps; ++s) {
+        const int so = s % C::NSO;
+        if (s >= C::NSO && !mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x13, s)) break;
+        mbar_arrive_expect_tx(full_a(so), C::OPA);
+        tma_load_2d(sbase + C::OFF_A + so * C::OPA, &tmapA,
+                    static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * QK),
+                    static_cast<int32_t>(m0), full_a(so));
+        issued = s + 1;
+      }
+      if (*abort_flag) {
+        for (int s = max(0, issued - C::NSO); s < issued; ++s)
+          drain_wait(full_a(s % C::NSO), (s / C::NSO) & 1, 100000000ull);
+      }
+    }
+  } else if (warp == WARP_MMA) {
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_e4m3_f32(256u, static_cast<uint32_t>(nq));
+      for (int s = 0; s < nsteps; ++s) {
+        const int so = s % C::NSO;
+        const int in_chain = s % QCHAIN;
+        if (s > 0 && in_chain == 0 &&
+            !mbar_wait(acc_empty, ((s / QCHAIN) - 1) & 1, ab, 0x25, s))
+          break;
+        if (!mbar_wait(full_o(so), (s / C::NSO) & 1, ab, 0x22, s)) break;
+        tc_fence_after();
+#pragma unroll
+        for (int ks = 0; ks < QK / 32; ++ks) {
+          const uint64_t bdesc =
+              smem_desc(sbase + C::OFF_S + so * C::OPS + static_cast<uint32_t>(ks) * 256u, 128u,
+                        1024u);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint64_t adesc = smem_desc_sw128(
+                sbase + C::OFF_A + so * C::OPA + static_cast<uint32_t>(j) * (C::OPA / 2) +
+                    static_cast<uint32_t>(ks) * 32u,
+                16u, 1024u);
+            mma_e4m3_pair(tmem + static_cast<uint32_t>(j * nq), adesc, bdesc, idesc,
+                          (in_chain > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit_pair_both(empty_o(so));
+        if (in_chain == QCHAIN - 1 || s == nsteps - 1) mma_commit_pair_both(acc_full);
+      }
+      mma_commit_pair(drain_bar);
+      drain_wait(drain_bar, 0, 200000000ull);
+    }
+  } else if (warp < WARP_WORK0) {
+    // ---- epilogue: accumulator j holds rows m0 + 128 j + lane, columns q0 + c ----
+    const int quarter = warp & 3;
+    const int colset = (warp - WARP_EPI0) >> 2;
+    const bool vec_ok = (p.Q % 4) == 0;
+    const int nchunk = (nq + 31) / 32;
+    for (int c0 = 0; c0 < nchains; ++c0) {
+      const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      for (int t = colset; t < 2 * nchunk; t += 2) {
+        const int j = t / nchunk;
+        const int ci = t - j * nchunk;
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                      static_cast<uint32_t>(j * nq + ci * 32),
+                  v);
+        tmem_ld_wait();
+        const int64_t gm = m0 + j * 128 + quarter * 32 + lane;
+        if (gm < p.P) {
+          const int e = p.exps[gm];  // the row's scale 2^e: an exact multiply
+          float* drow = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + q0;
+#pragma unroll
+          for (int u4 = 0; u4 < 32; u4 += 4) {
+            const int c = ci * 32 + u4;
+            if (c >= nq) continue;
+            const int64_t col = q0 + c;
+            const float a0 = ldexpf(__uint_as_float(v[u4]), e);
+            const float a1 = ldexpf(__uint_as_float(v[u4 + 1]), e);
+            const float a2 = ldexpf(__uint_as_float(v[u4 + 2]), e);
+            const float a3 = ldexpf(__uint_as_float(v[u4 + 3]), e);
+            float* d = drow + c;
+            if (vec_ok && col + 4 <= p.Q) {
+              if (c0 == 0)
+                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+              else
+                red_add_v4(d, a0, a1, a2, a3);
+            } else {
+              const float vv[4] = {a0, a1, a2, a3};
+              for (int u = 0; u < 4; ++u) {
+                if (col + u < p.Q) {
+                  if (c0 == 0)
+                    d[u] = vv[u];
+                  else
+                    red_add(d + u, vv[u]);
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
+    }
+  } else {
+    // ---- workers: this CTA's half of the E4M3 S tile [gh x 128] ----
+    const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
+    const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
+    for (int s = grp; s < nsteps; s += C::NGROUPS) {
+      const int so = s % C::NSO;
+      bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
+      const int64_t cbase = lbeg + static_cast<int64_t>(s) * QK;  // a multiple of 128
+      if (DIST == kRademacher) {
+        // one row per task: one Philox call covers the stage's 128 columns
+        for (int r = wt; r < gh; r += C::GROUP_THREADS) {
+          const int64_t grow = g0 + r;
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          int64_t nv = 0;
+          if (grow < p.Q && cbase < lend) {
+            w = rademacher_bits(p.key, static_cast<uint32_t>(grow),
+                                static_cast<uint32_t>(cbase >> 7), 0u);
+            nv = min(lend - cbase, static_cast<int64_t>(QK));
+          }
+          const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {  // 16-column blocks
+            const uint32_t bits = words[b >> 1] >> (16 * (b & 1));
+            uint32_t q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              q[u] = rad4_e4m3(bits >> (4 * u));
+              const int64_t c = 16 * b + 4 * u;  // columns past the split are zero
+              if (c + 4 > nv) {
+                uint32_t keep = 0u;
+                for (int e = 0; e < 4; ++e)
+                  if (c + e < nv) keep |= 0xFFu << (8 * e);
+                q[u] &= keep;
+              }
+            }
+            *reinterpret_cast<uint4*>(sdst + q8_off(static_cast<uint32_t>(r), 16u * b)) =
+                make_uint4(q[0], q[1], q[2], q[3]);
+          }
+        }
+      } else {
+        // per 32 tasks: 8 rows x 4 quads of one 16-column block
+        const int ntasks = gh * 32;
+        for (int t = wt; t < ntasks; t += C::GROUP_THREADS) {
+          const uint32_t l = static_cast<uint32_t>(t & 31);
+          const uint32_t w = static_cast<uint32_t>(t >> 5);
+          const uint32_t blk = w & 7u;
+          const uint32_t r = (w >> 3) * 8u + (l >> 2);
+          const uint32_t c = blk * 16u + (l & 3u) * 4u;
+          const int64_t grow = g0 + r;
+          const int64_t cc = cbase + c;
+          uint32_t q = 0u;
+          if (grow < p.Q && cc < lend) {
+            const float4 a = DIST == kUniform
+                                 ? uniform4(p.key, static_cast<uint32_t>(grow),
+                                            static_cast<uint32_t>(cc >> 2), 0u)
+                                 : gaussian4(p.key, static_cast<uint32_t>(grow),
+                                             static_cast<uint32_t>(cc >> 2), 0u);
+            q = e4m3x4(a);
+          }
+          *reinterpret_cast<uint32_t*>(sdst + q8_off(r, c)) = q;
+        }
+      }
+      ok = mbar_wait(full_a(so), (s / C::NSO) & 1, ab, 0x40, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      fence_proxy_async_smem();  // the S tile is read by the tensor core
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_full_o + 8u * so);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == WARP_MMA) {
+    tc_fence_after();
+    __syncwarp();
+    tmem_dealloc_pair(tmem, static_cast<uint32_t>(p.tmem_cols));
+  }
+}
+
+// Row exponent of a row with max |a| = amax: the smallest e with
+// amax <= 448 * 2^e (0 for a zero row or one holding Inf).  448 = 1.75 * 2^8,
+// so from ilogb(amax) - 8 at most one step is needed either way.
+__device__ __forceinline__ int e4m3_row_exponent(float amax) {
+  int e = 0;
+  if (amax > 0.0f && amax <= 3.4028235e38f) {
+    e = ilogbf(amax) - 8;
+    for (int it = 0; it < 4 && ldexpf(amax, -e) > 448.0f; ++it) ++e;
+    for (int it = 0; it < 4 && ldexpf(amax, 1 - e) <= 448.0f; ++it) --e;
+  }
+  return e;
+}
+
+// Quantize rows of A holding a whole row in registers: one 256-thread block
+// per row, VPT float4 per thread (n <= 1024 * VPT), rows 16-byte aligned; one
+// read of A, codes written once.
+template <int VPT>
+__global__ void __launch_bounds__(256)
+    k_quantize_rows_e4m3_regs(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                              uint8_t* __restrict__ Aq, int64_t ldq, int32_t* __restrict__ exps) {
+  __shared__ float wmax[8];
+  const int tid = threadIdx.x;
+  const int64_t nv = n / 4;  // whole float4 groups; the tail (n % 4) is read per element
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+    const float* a = A + r * lda;
+    float4 v[VPT];
+    float amax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+      const int64_t g = tid + 256 * i;  // float4 index
+      if (g < nv) {
+        v[i] = __ldcs(reinterpret_cast<const float4*>(a) + g);
+      } else {
+        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t c = 4 * g;
+        if (c < n) {  // the ragged tail
+          v[i].x = a[c];
+          if (c + 1 < n) v[i].y = a[c + 1];
+          if (c + 2 < n) v[i].z = a[c + 2];
+        }
+      }
+      amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[i].x), fabsf(v[i].y)),
+                               fmaxf(fabsf(v[i].z), fabsf(v[i].w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) wmax[tid >> 5] = amax;
+    __syncthreads();
+    amax = wmax[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) amax = fmaxf(amax, wmax[w]);
+    __syncthreads();  // wmax is rewritten by the next row
+    const int e = e4m3_row_exponent(amax);
+    if (tid == 0) exps[r] = e;
+    uint32_t* q = reinterpret_cast<uint32_t*>(Aq + r * ldq);
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+      const int64_t g = tid + 256 * i;
+      if (4 * g < ldq)
+        q[g] = e4m3x4(make_float4(ldexpf(v[i].x, -e), ldexpf(v[i].y, -e), ldexpf(v[i].z, -e),
+                                  ldexpf(v[i].w, -e)));
+    }
+  }
+}
+
+// Quantize rows of A: one warp per row finds max |a| (exact), the row
+// exponent e (the smallest with max |a| <= 448 * 2^e) and writes the codes
+// RNE_e4m3(a * 2^-e), zero-padded to ldq columns.  VEC: rows 16-byte aligned.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+    k_quantize_rows_e4m3(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                         uint8_t* __restrict__ Aq, int64_t ldq, int32_t* __restrict__ exps) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * 8;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); r < m;
+       r += warps) {
+    const float* a = A + r * lda;
+    float amax = 0.0f;
+    if (VEC) {
+      int64_t c = 4 * lane;
+      for (; c + 4 <= n; c += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(a + c);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+      for (int64_t t = n / 4 * 4 + lane; t < n; t += 32) amax = fmaxf(amax, fabsf(a[t]));
+    } else {
+      for (int64_t c = lane; c < n; c += 32) amax = fmaxf(amax, fabsf(a[c]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const int e = e4m3_row_exponent(amax);
+    if (lane == 0) exps[r] = e;
+    uint8_t* q = Aq + r * ldq;
+    for (int64_t c = 16 * lane; c < ldq; c += 512) {  // 16 codes per lane
+      float x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = c + u < n ? ldexpf(a[c + u], -e) : 0.0f;
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        w[u] = e4m3x4(make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]));
+      *reinterpret_cast<uint4*>(q + c) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int num_sms_tc() {
@@ -1352,6 +1766,58 @@ Plan plan_right(const GemmShape& s) {
   return pl;
 }
 
+// FP8 right sketch: the same tiling as the BF16 right sketch, splits of
+// whole 128-column stages.
+Plan plan_right_q(const GemmShape& s) {
+  Plan pl = plan_right(s);
+  int64_t chunk = (s.L + pl.splits - 1) / pl.splits;
+  chunk = (chunk + QK - 1) / QK * QK;
+  pl.chunk = chunk;
+  pl.splits = static_cast<int>((s.L + chunk - 1) / chunk);
+  return pl;
+}
+
+cudaError_t set_smem_attr_right_q() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_e4m3_right<kGaussian>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, CfgQ::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_e4m3_right<kRademacher>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CfgQ::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_e4m3_right<kUniform>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CfgQ::SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int DIST>
+cudaError_t launch_right_q(const CUtensorMap& map, const TcRightQParams& p, dim3 grid,
+                           cudaStream_t st) {
+  cudaError_t e = set_smem_attr_right_q();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config<true>(&cfg, attr, grid, st);
+  cfg.dynamicSmemBytes = CfgQ::SMEM;
+  return cudaLaunchKernelEx(&cfg, k_sketch_e4m3_right<DIST>, map, p);
+}
+
+// A_q[m x n] (row stride ldq bytes) as a 2D byte tensor; one box = 128 bytes
+// of 256 rows, 128-byte swizzle (the K-major operand layout of the kernel).
+bool encode_q8_map(CUtensorMap* map, const uint8_t* Aq, int64_t m, int64_t n, int64_t ldq) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(m)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ldq)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(QK), static_cast<cuuint32_t>(CfgQ::ROWS)};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(Aq), gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int DIST>
 cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 grid,
                          cudaStream_t st) {
@@ -1452,6 +1918,96 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   if (e != cudaSuccess) return e;
   count_launches(1);
   return splitk_reduce(static_cast<float*>(ws), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+}
+
+int64_t q8_ld(int64_t n) { return (n + 15) / 16 * 16; }
+
+cudaError_t q8_quantize(const float* A, int64_t lda, int64_t m, int64_t n, uint8_t* Aq,
+                        int64_t ldq, int32_t* exps, cudaStream_t st) {
+  const bool vec = (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && lda % 4 == 0;
+  if (vec && ldq <= 4096 * 4) {  // a row fits in the registers of one block
+    const int64_t blocks = std::min<int64_t>(m, static_cast<int64_t>(num_sms_tc()) * 8);
+    const unsigned g = static_cast<unsigned>(blocks);
+    if (ldq <= 1024)
+      k_quantize_rows_e4m3_regs<1><<<g, 256, 0, st>>>(A, lda, m, n, Aq, ldq, exps);
+    else if (ldq <= 4096)
+      k_quantize_rows_e4m3_regs<4><<<g, 256, 0, st>>>(A, lda, m, n, Aq, ldq, exps);
+    else
+      k_quantize_rows_e4m3_regs<16><<<g, 256, 0, st>>>(A, lda, m, n, Aq, ldq, exps);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  const int64_t blocks = std::min<int64_t>((m + 7) / 8, static_cast<int64_t>(num_sms_tc()) * 8);
+  if (vec)
+    k_quantize_rows_e4m3<true><<<static_cast<unsigned>(blocks), 256, 0, st>>>(A, lda, m, n, Aq,
+                                                                              ldq, exps);
+  else
+    k_quantize_rows_e4m3<false><<<static_cast<unsigned>(blocks), 256, 0, st>>>(A, lda, m, n, Aq,
+                                                                               ldq, exps);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+size_t q8_partial_bytes(const GemmShape& s) {
+  const Plan pl = plan_right_q(s);
+  return static_cast<size_t>(pl.splits) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
+         sizeof(float);
+}
+
+size_t q8_workspace_bytes(const GemmShape& s) {
+  const size_t codes = (static_cast<size_t>(s.P) * q8_ld(s.L) + 255) / 256 * 256;
+  const size_t exps = (static_cast<size_t>(s.P) * 4 + 255) / 256 * 256;
+  return codes + exps + q8_partial_bytes(s);
+}
+
+cudaError_t q8_sketch_right_quantized(const sk_sketch* h, const GemmShape& s, const uint8_t* Aq,
+                                      const int32_t* exps, int64_t ldq, float* Y, int64_t ldy,
+                                      void* part, size_t part_bytes, cudaStream_t st) {
+  const Plan pl = plan_right_q(s);
+  if (part == nullptr || part_bytes < q8_partial_bytes(s)) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  if (!encode_q8_map(&map, Aq, s.P, s.L, ldq)) return cudaErrorInvalidValue;
+  TcRightQParams p;
+  p.part = static_cast<float*>(part);
+  p.exps = exps;
+  p.P = s.P;
+  p.Q = s.Q;
+  p.L = s.L;
+  p.chunk = pl.chunk;
+  p.nq = pl.nt;
+  p.tmem_cols = pl.tmem_cols;
+  p.key = make_key(h->seed);
+  p.status = h->d_status;
+  p.timeout_ns = 2000000000ull;
+  dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
+            static_cast<unsigned>(pl.splits));
+  prof_mark(h->prof_start, st);
+  cudaError_t e;
+  if (h->dist == kRademacher)
+    e = launch_right_q<kRademacher>(map, p, grid, st);
+  else if (h->dist == kUniform)
+    e = launch_right_q<kUniform>(map, p, grid, st);
+  else
+    e = launch_right_q<kGaussian>(map, p, grid, st);
+  prof_mark(h->prof_stop, st);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  return splitk_reduce(static_cast<float*>(part), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+}
+
+cudaError_t q8_sketch_right(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                            float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (ws == nullptr || ws_bytes < q8_workspace_bytes(s)) return cudaErrorInvalidValue;
+  const int64_t ldq = q8_ld(s.L);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  uint8_t* Aq = w;
+  const size_t codes = (static_cast<size_t>(s.P) * ldq + 255) / 256 * 256;
+  int32_t* exps = reinterpret_cast<int32_t*>(w + codes);
+  const size_t eb = (static_cast<size_t>(s.P) * 4 + 255) / 256 * 256;
+  cudaError_t e = q8_quantize(A, lda, s.P, s.L, Aq, ldq, exps, st);
+  if (e != cudaSuccess) return e;
+  return q8_sketch_right_quantized(h, s, Aq, exps, ldq, Y, ldy, w + codes + eb,
+                                   ws_bytes - codes - eb, st);
 }
 
 cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,

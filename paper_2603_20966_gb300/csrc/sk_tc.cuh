@@ -140,9 +140,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          (1ull << 46);
 }
 
-// Descriptor of a 128-byte-swizzled operand (layout type 2): `lbo` = bytes
-// between swizzle atoms along M/N, `sbo` = bytes between 8-row groups along
-// K (MN-major operands, as loaded by a TMA box with SWIZZLE_128B).
+// Descriptor of a 128-byte-swizzled operand (layout type 2).  MN-major (as
+// loaded by a TMA box with SWIZZLE_128B): `lbo` = bytes between swizzle atoms
+// along M/N, `sbo` = bytes between 8-row groups along K.  K-major (rows of
+// 128 B): `sbo` = bytes between 8-row groups, `lbo` unused; successive K
+// steps start 32 B further into the row.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) |
          (static_cast<uint64_t>(lbo >> 4) << 16) | (static_cast<uint64_t>(sbo >> 4) << 32) |
@@ -245,6 +247,21 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, u
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// One kind::f8f6f4 MMA (E4M3 x E4M3 -> FP32) across the CTA pair.
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format 0), FP32 D,
+// both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
 // Arrive on `bar` in both CTAs of the pair once the pair's MMAs completed.
 __device__ __forceinline__ void mma_commit_pair_both(uint32_t bar) {
   asm volatile(
