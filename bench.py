@@ -114,23 +114,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measured_traffic():
-    """DRAM bytes per benchmarked launch of the fused kernel from the committed
-    ncu summary, or None when the kernel source changed since the capture."""
+def left_kernel_source_sha() -> str | None:
+    """Hash of the left sketch's device code (constants, split pass, worker,
+    epilogue and MMA code of sk_tc.cu up to the right sketch), which the
+    committed ncu summary records; an edit elsewhere does not invalidate it."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_sketch_bf16x2_left_pair_m2e18.md")
     src = os.path.join(ROOT, "paper_2603_20966_gb300", "csrc", "sk_tc.cu")
     try:
-        text = open(prof).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(src).read()
     except OSError:
         return None
+    i0, i1 = text.find("constexpr int BM = 128;"), text.find("// Right sketch Y[m x k]")
+    if i0 < 0 or i1 < 0:
+        return None
+    return hashlib.sha256(text[i0:i1].encode()).hexdigest()[:16]
+
+
+def measured_traffic(dist: int):
+    """DRAM bytes of one benchmarked sketch (split pass + sketch kernel) of
+    distribution `dist` from the committed ncu summary, or None when the
+    left kernel's source changed since the capture."""
+    prof = os.path.join(ROOT, "profiles", "k_sketch_bf16x2_left_pair_m2e18.md")
+    sha = left_kernel_source_sha()
+    try:
+        text = open(prof).read()
+    except OSError:
+        return None
+    key = f"traffic_bytes_per_full_sketch_{DIST_NAME[dist]}"
     rec = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and
-               line.split(": ", 1)[0] in ("kernel_source_sha256_16", "traffic_bytes_per_full_launch"))
-    if rec.get("kernel_source_sha256_16") != sha:
+               line.split(": ", 1)[0] in ("left_kernel_source_sha256_16", key))
+    if sha is None or rec.get("left_kernel_source_sha256_16") != sha:
         return None
     try:
-        return float(rec["traffic_bytes_per_full_launch"])
+        return float(rec[key])
     except (KeyError, ValueError):
         return None
 
@@ -484,6 +500,10 @@ def run_ours(args):
     if world > 1:
         tdist.init_process_group("nccl", device_id=dev)
     m, n, k, dists, side = WORKLOADS[args.workload]
+    if args.rows is not None:  # a smaller case of the same workload (profiling captures)
+        m = args.rows
+    if args.dists is not None:
+        dists = tuple(int(x) for x in args.dists.split(","))
     form = {"fp32": P.SK_FP32, "bf16x2": P.SK_BF16X2, "fp8": P.SK_FP8E4M3}[args.form]
     if form == P.SK_FP8E4M3 and side != "right":
         raise SystemExit("the FP8 form is the right sketch only (workload C3)")
@@ -588,7 +608,14 @@ def run_ours(args):
                 "unit": "TFLOP/s", "peak_kind": f"{pk_kind} bf16 burst",
                 "note": "achieved counts both split-A MMA passes (4 k m n flop per sketch)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = measured_traffic() if (form != P.SK_FP32 and args.workload == "C2") else None
+    if form == P.SK_BF16X2 and side == "left" and args.rows is None:
+        tr = [measured_traffic(d) for d in dists]
+        roof["traffic"] = None if any(t is None for t in tr) else sum(tr) / len(tr)
+        if roof["traffic"] is not None:
+            roof["traffic_note"] = ("DRAM bytes per sketch (split pass + sketch kernel, average "
+                                    "over the distributions) from the committed ncu summary")
+    else:
+        roof["traffic"] = None
     roof["kernel_ms_by_dist"] = {DIST_NAME[d]: statistics.mean(kernel_ms[j::len(dists)])
                                  for j, d in enumerate(dists)}
 
@@ -699,6 +726,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--rows", type=int, default=None,
+                    help="rows of A (C1-C3): a smaller case of the workload, for ncu captures")
+    ap.add_argument("--dists", default=None, help="comma-separated distributions (0 G, 1 R, 2 U)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
