@@ -233,3 +233,17 @@ def apply_right_q8(seed: int, dist: int, k: int, codes: np.ndarray, exps: np.nda
     if rc != 0:
         raise ValueError("orc_apply_right_q8 failed")
     return Y
+
+
+def nystrom(seed: int, dist: int, prec: int, k: int, A: np.ndarray, nthreads: int | None = None):
+    """The two products of the paper's Nystrom computation (Sec. 5, Alg. 2),
+    B = A Omega and C = Omega^T B with Omega = S^T (S[k x n] the sketching
+    matrix, k = r), in FP64: B[n x k] by the right sketch, then C[k x k] as
+    S B with S's exact values (a library matmul as the step)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("A must be square")
+    Bm = apply_right(seed, dist, prec, k, A, nthreads=nthreads)
+    S = materialize_scaled(seed, dist, prec, k, 0, 0, k, n)
+    return Bm, S @ Bm
