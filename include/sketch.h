@@ -117,7 +117,19 @@ sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64
 sk_status sk_apply_right(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
                          float* Y, int64_t ldy, void* stream);
 
-/* E4M3 form of A for the FP8 right sketch: row_exp[i] = the smallest integer
+/* The two products of a Nystrom approximation (the paper's Sec. 5, Alg. 2
+ * RandCompNys on one device): B[n x k] = A Omega and C[k x k] = Omega^T B,
+ * Omega = S^T the handle's n x k random matrix (k = r), for a symmetric
+ * A[n x n] (not checked).  Runs the right sketch of A into B, then the left
+ * sketch of B into C, both regenerating the same S; the Nystrom
+ * approximation is then B C^+ B^T.  Conventions of sk_apply_left /
+ * sk_apply_right (B is the second product's input: the tensor-core form
+ * needs it 16-byte aligned with ldb a multiple of 4).  Errors as those
+ * calls; SK_EUNSUPPORTED in the SK_FP8E4M3 form. */
+sk_status sk_nystrom(sk_handle h, const float* A, int64_t n, int64_t lda, float* B, int64_t ldb,
+                     float* C, int64_t ldc, void* stream);
+
+/* E4M3 form of A for the FP8 right sketch:/* E4M3 form of A for the FP8 right sketch: row_exp[i] = the smallest integer
  * e with max_j |A[i][j]| <= 448 * 2^e (0 for a row of zeros), and
  * Aq[i*ldq + j] = RNE_e4m3(A[i][j] * 2^-e) for j < n (OCP E4M3, largest 448,
  * no code saturates), 0 for n <= j < ldq.  A: device FP32, leading dim

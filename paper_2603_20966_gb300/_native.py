@@ -45,6 +45,7 @@ PROTOTYPES = {
     "sk_batch_status": (_int, [_vp, _vp]),
     "sk_batch_size": (_int, [_vp, _P(_i64)]),
     "sk_batch_destroy": (_int, [_vp]),
+    "sk_nystrom": (_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp]),
     "sk_quantize_e4m3": (_int, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
     "sk_apply_right_e4m3": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_server_create": (_int, [_u64, ctypes.c_int32, _P(_vp)]),
@@ -342,3 +343,9 @@ def sk_apply_right_e4m3(h, Aq, row_exp, m, n, ldq, Y, ldy, stream=None) -> None:
     _check("sk_apply_right_e4m3", _lib.sk_apply_right_e4m3(h, _ptr(Aq), _ptr(row_exp), int(m),
                                                            int(n), int(ldq), _ptr(Y), int(ldy),
                                                            _stream(stream)))
+
+
+def sk_nystrom(h, A, n, lda, B, ldb, C, ldc, stream=None) -> None:
+    """B = A Omega, C = Omega^T B (see sketch.h)."""
+    _check("sk_nystrom", _lib.sk_nystrom(h, _ptr(A), int(n), int(lda), _ptr(B), int(ldb), _ptr(C),
+                                         int(ldc), _stream(stream)))

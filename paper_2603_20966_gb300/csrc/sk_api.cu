@@ -218,6 +218,17 @@ sk_status sk_materialize(sk_handle h, int64_t row0, int64_t col0, int64_t rows, 
                                    static_cast<cudaStream_t>(stream)));
 }
 
+sk_status sk_nystrom(sk_handle h, const float* A, int64_t n, int64_t lda, float* B, int64_t ldb,
+                     float* C, int64_t ldc, void* stream) {
+  if (!h || !A || !B || !C || n <= 0 || lda < n || ldb < h->k || ldc < h->k) return SK_EINVAL;
+  if (h->prec == SK_FP8E4M3) return SK_EUNSUPPORTED;  // the second product is a left sketch
+  // B[n x k] = A Omega (right sketch), then C[k x k] = Omega^T B = S B (left
+  // sketch of B): the same S, regenerated by both kernels
+  const sk_status st = apply(h, A, n, n, lda, B, ldb, stream, false);
+  if (st != SK_OK) return st;
+  return apply(h, B, n, h->k, ldb, C, ldc, stream, true);
+}
+
 sk_status sk_quantize_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, uint8_t* Aq,
                            int64_t ldq, int32_t* row_exp, void* stream) {
   if (!A || !Aq || !row_exp || m <= 0 || n <= 0 || lda < n || ldq < n || ldq % 16 != 0)

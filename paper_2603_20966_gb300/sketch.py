@@ -71,6 +71,17 @@ class Sketch:
                          torch.cuda.current_stream(A.device))
         return Y
 
+    def nystrom(self, A: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+        """(B, C) = (A Omega, Omega^T A Omega) for a symmetric n x n A."""
+        self._check(A)
+        n = A.shape[0]
+        ld = (self.k + 3) // 4 * 4
+        B = torch.empty((n, ld), dtype=torch.float32, device=A.device)
+        C = torch.empty((self.k, ld), dtype=torch.float32, device=A.device)
+        N.sk_nystrom(self.handle, A, n, A.stride(0), B, ld, C, ld,
+                     torch.cuda.current_stream(A.device))
+        return B[:, :self.k], C[:, :self.k]
+
     def materialize(self, row0: int, col0: int, rows: int, cols: int, fmt: int = N.SK_FP32,
                     scaled: bool = False, device="cuda") -> torch.Tensor:
         dt = {N.SK_FP32: torch.float32, N.SK_BF16X2: torch.bfloat16,
