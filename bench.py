@@ -645,6 +645,48 @@ def run_ours(args):
                        "by tests/test_gpu_fp8.py (about 3-4 %)"}
         del Aq, ex
 
+    # generate versus communicate (Sec. 6.2): the same kernel reading a
+    # materialized BF16 S from HBM instead of generating it
+    ablation = None
+    if form == P.SK_BF16X2 and side == "left" and not args.no_ablation:
+        lds = (m + 15) // 16 * 16
+        ablation = {"S_bytes": 2 * k * lds, "fused_kernel_ms": {}, "stored_kernel_ms": {},
+                    "materialize_ms": {}, "identical_to_fused": {},
+                    "note": "stored = sk_apply_left_stored reading S (materialized once by "
+                            "sk_materialize, BF16) by TMA in place of generating it; "
+                            "kernel times bracket the split pass and the sketch kernel, as "
+                            "for the fused path"}
+        for j, d in enumerate(dists):
+            S = torch.zeros((k, lds), dtype=torch.bfloat16, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.sk_materialize(hs[d], 0, 0, k, m, P.SK_BF16X2, 0, S, lds, stream)
+            e1.record(stream)
+            Yst = torch.empty(yshape, dtype=torch.float32, device=dev)
+            reps = max(3, min(args.steps, 10))
+            sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            for a, b in sev:
+                a.record(stream)
+                b.record(stream)
+            P.sk_apply_left_stored(hs[d], S, lds, A, m, n, n, Yst, yshape[1], stream)  # warm
+            for a, b in sev:
+                P.sk_profile_events(hs[d], a, b)
+                P.sk_apply_left_stored(hs[d], S, lds, A, m, n, n, Yst, yshape[1], stream)
+            P.sk_profile_events(hs[d], None, None)
+            torch.cuda.synchronize(dev)
+            st = P.sk_stream_status(hs[d], stream)
+            if st != 0:
+                raise RuntimeError(f"device status after the stored-S sketch: "
+                                   f"{P.status_string(st)}")
+            name = DIST_NAME[d]
+            ablation["materialize_ms"][name] = e0.elapsed_time(e1)
+            ablation["stored_kernel_ms"][name] = statistics.mean(a.elapsed_time(b)
+                                                                 for a, b in sev)
+            ablation["fused_kernel_ms"][name] = roof["kernel_ms_by_dist"][name]
+            ablation["identical_to_fused"][name] = bool(torch.equal(Yst, Ys[d]))
+            del S, Yst
+
     # end to end through the host-buffer entry points
     e2e = None
     if not args.no_e2e:
@@ -709,6 +751,8 @@ def run_ours(args):
         }
         if fp8 is not None:
             line["fp8"] = fp8
+        if ablation is not None:
+            line["gen_vs_comm"] = ablation
         print(json.dumps(line), flush=True)
     if world > 1:
         tdist.destroy_process_group()
@@ -725,6 +769,8 @@ def main():
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the stored-S (generate versus communicate) comparison")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--rows", type=int, default=None,
                     help="rows of A (C1-C3): a smaller case of the workload, for ncu captures")

@@ -129,7 +129,24 @@ sk_status sk_apply_right(sk_handle h, const float* A, int64_t m, int64_t n, int6
 sk_status sk_nystrom(sk_handle h, const float* A, int64_t n, int64_t lda, float* B, int64_t ldb,
                      float* C, int64_t ldc, void* stream);
 
-/* E4M3 form of A for the FP8 right sketch:/* E4M3 form of A for the FP8 right sketch: row_exp[i] = the smallest integer
+/* The left sketch of sk_apply_left in the SK_BF16X2 form with S read from
+ * memory instead of generated: the "communicate Omega" side of the paper's
+ * trade between generating the random matrix and moving it (Sec. 6.2,
+ * generation versus communication), kept to measure that trade on one GPU.
+ * S: device BF16 (raw 16-bit words), row r < k at S + r * lds, columns
+ * c < m; sk_materialize(h, 0, 0, k, m, SK_BF16X2, 0, S, lds) writes the
+ * handle's own S, for which Y equals sk_apply_left's bit for bit (Y is
+ * s S A with s the handle's 1/sqrt(k), whatever S holds).  The
+ * kernel reads S in 16-column slabs: columns m .. round_up(m, 16) - 1 of
+ * every row are read too and must hold finite values (multiplied by zero).
+ * Requires the handle in the SK_BF16X2 form (else SK_EUNSUPPORTED), k and
+ * lds multiples of 8, lds >= round_up(m, 16), S 16-byte aligned, and the
+ * alignment rules of sk_apply_left's tensor-core forms (else SK_EINVAL).
+ * The caller owns S; it is read asynchronously on `stream`. */
+sk_status sk_apply_left_stored(sk_handle h, const void* S, int64_t lds, const float* A, int64_t m,
+                               int64_t n, int64_t lda, float* Y, int64_t ldy, void* stream);
+
+/* E4M3 form of A for the FP8 right sketch: row_exp[i] = the smallest integer
  * e with max_j |A[i][j]| <= 448 * 2^e (0 for a row of zeros), and
  * Aq[i*ldq + j] = RNE_e4m3(A[i][j] * 2^-e) for j < n (OCP E4M3, largest 448,
  * no code saturates), 0 for n <= j < ldq.  A: device FP32, leading dim

@@ -45,6 +45,7 @@ PROTOTYPES = {
     "sk_batch_status": (_int, [_vp, _vp]),
     "sk_batch_size": (_int, [_vp, _P(_i64)]),
     "sk_batch_destroy": (_int, [_vp]),
+    "sk_apply_left_stored": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "sk_nystrom": (_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp]),
     "sk_quantize_e4m3": (_int, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
     "sk_apply_right_e4m3": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp]),
@@ -180,6 +181,14 @@ def sk_apply_left_noalloc(h, A, m, n, lda, Y, ldy, stream=None):
     """FP32 left sketch whose scratch is a fixed array inside the library:
     for callers that must not have this library allocate device memory."""
     _apply("sk_apply_left_noalloc", h, A, m, n, lda, Y, ldy, stream)
+
+
+def sk_apply_left_stored(h, S, lds, A, m, n, lda, Y, ldy, stream=None):
+    """BF16 left sketch reading a caller-stored BF16 S instead of generating
+    it (the communicated-S side of the generate-vs-communicate trade)."""
+    _check("sk_apply_left_stored",
+           _lib.sk_apply_left_stored(h, _ptr(S), int(lds), _ptr(A), int(m), int(n), int(lda),
+                                     _ptr(Y), int(ldy), _stream(stream)))
 
 
 def sk_apply_left_host(h, A, m, n, lda, Y, ldy, stream=None):

@@ -229,6 +229,28 @@ sk_status sk_nystrom(sk_handle h, const float* A, int64_t n, int64_t lda, float*
   return apply(h, B, n, h->k, ldb, C, ldc, stream, true);
 }
 
+sk_status sk_apply_left_stored(sk_handle h, const void* S, int64_t lds, const float* A,
+                              int64_t m, int64_t n, int64_t lda, float* Y, int64_t ldy,
+                              void* stream) {
+  sk_status st = check_apply(h, A, m, n, lda, Y, ldy, true);
+  if (st != SK_OK) return st;
+  if (h->prec != SK_BF16X2) return SK_EUNSUPPORTED;
+  if (!S || h->k % 8 != 0 || lds % 8 != 0 || lds < (m + 15) / 16 * 16 ||
+      (reinterpret_cast<uintptr_t>(S) & 15u))
+    return SK_EINVAL;
+  GemmShape s;
+  s.left = true;
+  s.P = h->k;
+  s.Q = n;
+  s.L = m;
+  st = sk::tc_check(s, A, lda, Y, ldy);
+  if (st != SK_OK) return st;
+  st = ensure_workspace(h, workspace_for(h, s));
+  if (st != SK_OK) return st;
+  return from_cuda(sk::tc_sketch_left_stored(h, s, S, lds, A, lda, Y, ldy, h->ws, h->ws_bytes,
+                                             static_cast<cudaStream_t>(stream)));
+}
+
 sk_status sk_quantize_e4m3(const float* A, int64_t m, int64_t n, int64_t lda, uint8_t* Aq,
                            int64_t ldq, int32_t* row_exp, void* stream) {
   if (!A || !Aq || !row_exp || m <= 0 || n <= 0 || lda < n || ldq < n || ldq % 16 != 0)

@@ -25,7 +25,7 @@ struct sk_sketch {
   cudaEvent_t prof_stop;
   void* d_sched;           // device copy of the tensor-core work list (problem + items)
   size_t d_sched_bytes;
-  uint64_t sched_key[8];   // what the uploaded work list was built for
+  uint64_t sched_key[9];   // what the uploaded work list was built for
 };
 
 namespace sk {
@@ -126,6 +126,10 @@ size_t tc_workspace_bytes(const GemmShape& s);
 sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float* Y, int64_t ldy);
 cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                       float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
+// the same left sketch reading a caller-stored BF16 S[k x m] (row stride lds)
+cudaError_t tc_sketch_left_stored(const sk_sketch* h, const GemmShape& s, const void* S,
+                                  int64_t lds, const float* A, int64_t lda, float* Y,
+                                  int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st);
 
 // ---- FP8 (E4M3) form of the right sketch (sk_tc.cu) ----
 int64_t q8_ld(int64_t n);  // row stride (bytes) of the codes of an n-column A

@@ -132,7 +132,8 @@ constexpr uint32_t B_KSTEP = BK * HCHUNK * 2;       // 2048: next 16 rows of m
 // One left-sketch problem of a launch (a single sketch, or one member of a
 // batch).  Lives in device memory; the tensor map must be 64-byte aligned.
 struct alignas(128) LeftProblem {
-  CUtensorMap map;  // split A: {64 columns, m rows, chunks, hi/lo}, box {64, 16, cols/64, 2}
+  CUtensorMap map;   // split A: {64 columns, m rows, chunks, hi/lo}, box {64, 32, cols/64, 2}
+  CUtensorMap smap;  // stored S (kStored only): the S tile of a stage in its operand layout
   float* part;      // partials [splits][P][Q] of this problem
   int64_t P, Q, L;  // P = k, Q = n, L = m
   int64_t chunk;    // contracted length per split (multiple of LK)
@@ -382,8 +383,12 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
 // Persistent left-sketch kernel: each pair (or single CTA) runs its list of
 // items back to back; ring positions, barrier phases and accumulation chains
 // are counted across items (g = stage counter, gc = chain counter).  DIST is
-// the distribution of every item, or kMixed to read it per item (batches).
+// the distribution of every item, kMixed to read it per item (batches), or
+// kStored to read a caller-materialized BF16 S by TMA instead of generating
+// it (the "communicate Omega" side of the paper's Sec. 6.2 trade, for
+// measurement).
 constexpr int kMixed = -1;
+constexpr int kStored = 3;
 
 template <int DIST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -453,7 +458,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const CUtensorMap* map = &ig.pr->map;
         tma_prefetch_desc(map);
-        const uint32_t tx = static_cast<uint32_t>(2 * ig.cols * LK * 2);  // hi + lo
+        if (DIST == kStored) tma_prefetch_desc(&ig.pr->smap);
+        const uint32_t tx = static_cast<uint32_t>(2 * ig.cols * LK * 2) +  // hi + lo
+                            (DIST == kStored ? C::OPS : 0u);               // + the S tile
         const int32_t z0 =
             static_cast<int32_t>((ig.q0 + static_cast<int64_t>(rank) * ig.cols) / HCHUNK);
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
@@ -463,6 +470,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mbar_arrive_expect_tx(full_b(so), tx);
           const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * LK);
           tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
+          if (DIST == kStored)  // S rows p0.., columns y.. of the stage, in the operand layout
+            tma_load_5d(sbase + C::OFF_S + so * C::OPS, &ig.pr->smap, 0, 0, 0,
+                        static_cast<int32_t>(ig.p0 / 8), y / 16, full_b(so));
           issued = g + 1;
         }
       }
@@ -653,14 +663,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
         const int64_t cbase = ig.lbeg + static_cast<int64_t>(s) * LK;
-        if (DIST != kMixed)
+        if constexpr (DIST == kStored) {
+          // the S tile arrives with the split A tile
+        } else if constexpr (DIST != kMixed) {
           gen_stage<DIST, C>(sdst, ig, cbase, wt, cached_blk, words);
-        else if (ig.dist == kRademacher)
-          gen_stage<kRademacher, C>(sdst, ig, cbase, wt, cached_blk, words);
-        else if (ig.dist == kUniform)
-          gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
-        else
-          gen_stage<kGaussian, C>(sdst, ig, cbase, wt, cached_blk, words);
+        } else {
+          if (ig.dist == kRademacher)
+            gen_stage<kRademacher, C>(sdst, ig, cbase, wt, cached_blk, words);
+          else if (ig.dist == kUniform)
+            gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
+          else
+            gen_stage<kGaussian, C>(sdst, ig, cbase, wt, cached_blk, words);
+        }
         // this CTA's split A tile of the stage has landed
         ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x40, g);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -1673,6 +1687,7 @@ cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
 
 template <bool PAIR>
 cudaError_t launch_left_dist(int dist, const LeftSched& sc, int64_t units, cudaStream_t st) {
+  if (dist == kStored) return launch_left<kStored, PAIR>(sc, units, st);
   if (dist == kRademacher) return launch_left<kRademacher, PAIR>(sc, units, st);
   if (dist == kUniform) return launch_left<kUniform, PAIR>(sc, units, st);
   return launch_left<kGaussian, PAIR>(sc, units, st);
@@ -1694,6 +1709,25 @@ bool encode_split_map(CUtensorMap* map, const void* H, int64_t m, int64_t n, int
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(H), gdim, gstride, box,
              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A caller-stored BF16 S[k x m] (row stride lds elements) as a 5D tensor
+// {8 columns, row % 8, 8-column half of a 16-column slab, row / 8, slab}: one
+// box {8, 8, 2, 16, 2} is the S tile of a stage (128 rows x 32 columns) in
+// the kernel's K-major no-swizzle operand layout.  k % 8 == 0; rows of S
+// beyond k are outside the tensor (zeros); lds >= m rounded up to 16.
+bool encode_stored_map(CUtensorMap* map, const void* S, int64_t k, int64_t m, int64_t lds) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t gdim[5] = {8, 8, 2, static_cast<cuuint64_t>(k / 8),
+                              static_cast<cuuint64_t>((m + 15) / 16)};
+  const cuuint64_t row = static_cast<cuuint64_t>(lds) * 2;
+  const cuuint64_t gstride[4] = {row, 16, 8 * row, 32};
+  const cuuint32_t box[5] = {8, 8, 2, static_cast<cuuint32_t>(BM / 8), LK / 16};
+  const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(S), gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
@@ -2014,9 +2048,13 @@ cudaError_t q8_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
                                    ws_bytes - codes - eb, st);
 }
 
-cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
-                      float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (!s.left) return tc_sketch_right(h, s, A, lda, Y, ldy, ws, ws_bytes, st);
+namespace {
+
+// The BF16 left sketch: split pass, then the persistent kernel generating S
+// (S_stored null) or reading the caller's BF16 S (row stride lds).
+cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                           float* Y, int64_t ldy, void* ws, size_t ws_bytes, const void* S_stored,
+                           int64_t lds, cudaStream_t st) {
   const LeftPlan pl = plan_left(s);
   const size_t sb = split_bytes(s.L, s.Q);
   const size_t need = sb + static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
@@ -2025,15 +2063,17 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + sb);
   sk_sketch* hm = const_cast<sk_sketch*>(h);
   // The work list depends only on these; upload it again only when they change.
-  const uint64_t key[8] = {reinterpret_cast<uint64_t>(A), static_cast<uint64_t>(s.L),
+  const uint64_t key[9] = {reinterpret_cast<uint64_t>(A), static_cast<uint64_t>(s.L),
                            static_cast<uint64_t>(s.Q), static_cast<uint64_t>(lda),
                            reinterpret_cast<uint64_t>(ws), h->seed,
                            static_cast<uint64_t>(h->dist) | (static_cast<uint64_t>(h->k) << 8),
-                           1u};
+                           reinterpret_cast<uint64_t>(S_stored), static_cast<uint64_t>(lds)};
   const int64_t units = pl.pair ? pair_slots() / 2 : num_sms_tc();
   HostSched hs;
   hs.probs.resize(1);
   if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist))
+    return cudaErrorInvalidValue;
+  if (S_stored && !encode_stored_map(&hs.probs[0].smap, S_stored, s.P, s.L, lds))
     return cudaErrorInvalidValue;
   build_items(std::vector<LeftPlan>{pl}, units, &hs);
   pack_sched(&hs);
@@ -2050,13 +2090,28 @@ cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, in
   prof_mark(h->prof_start, st);
   cudaError_t e = split_launch_one(A, lda, s.L, s.Q, H, st);
   if (e != cudaSuccess) return e;
-  e = pl.pair ? launch_left_dist<true>(h->dist, sc, nunits, st)
-              : launch_left_dist<false>(h->dist, sc, nunits, st);
+  const int mode = S_stored ? kStored : h->dist;
+  e = pl.pair ? launch_left_dist<true>(mode, sc, nunits, st)
+              : launch_left_dist<false>(mode, sc, nunits, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
   // fixed-order sum of the split partials, times 1/sqrt(k), into Y
   return splitk_reduce(part, pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+}
+
+}  // namespace
+
+cudaError_t tc_sketch(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
+                      float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!s.left) return tc_sketch_right(h, s, A, lda, Y, ldy, ws, ws_bytes, st);
+  return tc_sketch_left(h, s, A, lda, Y, ldy, ws, ws_bytes, nullptr, 0, st);
+}
+
+cudaError_t tc_sketch_left_stored(const sk_sketch* h, const GemmShape& s, const void* S,
+                                  int64_t lds, const float* A, int64_t lda, float* Y,
+                                  int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
+  return tc_sketch_left(h, s, A, lda, Y, ldy, ws, ws_bytes, S, lds, st);
 }
 
 struct PlannedBatch {
