@@ -124,12 +124,88 @@ __device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb) {
   return make_float2(__fmul_rn(rho, cs), __fmul_rn(rho, sn));
 }
 
+// ---- the same two Box-Muller transforms, evaluated side by side ----
+// Every step below is the scalar step above applied to the two pairs of one
+// Philox call at once: __fadd2_rn / __fmul2_rn / __ffma2_rn round each
+// component exactly like __fadd_rn / __fmul_rn / __fmaf_rn, so the results
+// are bit-identical to box_muller(x0, x1), box_muller(x2, x3) while the
+// floating-point work takes half the instructions (the generator is
+// instruction-issue bound inside the sketch kernels).  Integer steps,
+// division, square root and rounding to integer stay per component.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ float2 ln01_x2(float2 x) {
+  const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
+  int e0 = (int)(b0 >> 23) - 127, e1 = (int)(b1 >> 23) - 127;
+  uint32_t m0 = b0 & 0x007fffffu, m1 = b1 & 0x007fffffu;
+  if (m0 > 0x003504f3u) {
+    m0 |= 0x3f000000u;
+    e0 += 1;
+  } else {
+    m0 |= 0x3f800000u;
+  }
+  if (m1 > 0x003504f3u) {
+    m1 |= 0x3f000000u;
+    e1 += 1;
+  } else {
+    m1 |= 0x3f800000u;
+  }
+  const float2 f = f2(__uint_as_float(m0), __uint_as_float(m1));
+  const float2 num = __fadd2_rn(f, f2(-1.0f, -1.0f));
+  const float2 den = __fadd2_rn(f, f2(1.0f, 1.0f));
+  const float2 sv = f2(__fdiv_rn(num.x, den.x), __fdiv_rn(num.y, den.y));
+  const float2 s2 = __fmul2_rn(sv, sv);
+  float2 p = __ffma2_rn(s2, f2(0x1.c71c72p-3f, 0x1.c71c72p-3f), f2(0x1.24924ap-2f, 0x1.24924ap-2f));
+  p = __ffma2_rn(s2, p, f2(0x1.99999ap-2f, 0x1.99999ap-2f));
+  p = __ffma2_rn(s2, p, f2(0x1.555556p-1f, 0x1.555556p-1f));
+  const float2 s3 = __fmul2_rn(sv, s2);
+  const float2 lnf = __ffma2_rn(s3, p, __fadd2_rn(sv, sv));
+  const float2 ef = f2(__int2float_rn(e0), __int2float_rn(e1));
+  return __ffma2_rn(ef, f2(0x1.62e4p-1f, 0x1.62e4p-1f),
+                    __ffma2_rn(ef, f2(0x1.7f7d1cp-20f, 0x1.7f7d1cp-20f), lnf));
+}
+
+__device__ __forceinline__ void sincospi_x2(float2 t, float2* sn_out, float2* cs_out) {
+  const float2 tt = __fadd2_rn(t, t);
+  const float2 qf = f2(rintf(tt.x), rintf(tt.y));
+  const int q0 = (int)qf.x & 3, q1 = (int)qf.y & 3;
+  // t - q/2: the product q * 0.5 is exact, so one rounding as in the scalar form
+  const float2 r = __ffma2_rn(qf, f2(-0.5f, -0.5f), t);
+  const float2 r2 = __fmul2_rn(r, r);
+  float2 sp = __ffma2_rn(r2, f2(0x1.507834p-4f, 0x1.507834p-4f), f2(-0x1.32d2ccp-1f, -0x1.32d2ccp-1f));
+  sp = __ffma2_rn(r2, sp, f2(0x1.466bc6p+1f, 0x1.466bc6p+1f));
+  sp = __ffma2_rn(r2, sp, f2(-0x1.4abbcep+2f, -0x1.4abbcep+2f));
+  sp = __ffma2_rn(r2, sp, f2(0x1.921fb6p+1f, 0x1.921fb6p+1f));
+  const float2 sn = __fmul2_rn(r, sp);
+  float2 cp = __ffma2_rn(r2, f2(-0x1.a6d1f2p-6f, -0x1.a6d1f2p-6f), f2(0x1.e1f506p-3f, 0x1.e1f506p-3f));
+  cp = __ffma2_rn(r2, cp, f2(-0x1.55d3c8p+0f, -0x1.55d3c8p+0f));
+  cp = __ffma2_rn(r2, cp, f2(0x1.03c1f0p+2f, 0x1.03c1f0p+2f));
+  cp = __ffma2_rn(r2, cp, f2(-0x1.3bd3ccp+2f, -0x1.3bd3ccp+2f));
+  const float2 cs = __ffma2_rn(r2, cp, f2(1.0f, 1.0f));
+  const float a0 = (q0 & 1) ? cs.x : sn.x, b0 = (q0 & 1) ? sn.x : cs.x;
+  const float a1 = (q1 & 1) ? cs.y : sn.y, b1 = (q1 & 1) ? sn.y : cs.y;
+  *sn_out = f2((q0 == 2 || q0 == 3) ? -a0 : a0, (q1 == 2 || q1 == 3) ? -a1 : a1);
+  *cs_out = f2((q0 == 1 || q0 == 2) ? -b0 : b0, (q1 == 1 || q1 == 2) ? -b1 : b1);
+}
+
+// box_muller(x.x, x.y) and box_muller(x.z, x.w), as (z0, z1, z2, z3).
+__device__ __forceinline__ float4 box_muller_x2(uint4 x) {
+  const float2 k24 = f2(0x1p-24f, 0x1p-24f);
+  const float2 u1 = __fmul2_rn(f2(__uint2float_rn((x.x >> 8) + 1u), __uint2float_rn((x.z >> 8) + 1u)),
+                               k24);
+  const float2 u2 = __fmul2_rn(f2(__uint2float_rn(x.y >> 8), __uint2float_rn(x.w >> 8)), k24);
+  const float2 v = __fmul2_rn(f2(-2.0f, -2.0f), ln01_x2(u1));
+  const float2 rho = f2(__fsqrt_rn(v.x), __fsqrt_rn(v.y));
+  float2 sn, cs;
+  sincospi_x2(__fadd2_rn(u2, u2), &sn, &cs);
+  const float2 zc = __fmul2_rn(rho, cs);
+  const float2 zs = __fmul2_rn(rho, sn);
+  return make_float4(zc.x, zs.x, zc.y, zs.y);
+}
+
 // The four Gaussian entries (r, 4j .. 4j+3).
 __device__ __forceinline__ float4 gaussian4(PhiloxKey key, uint32_t r, uint32_t j, uint32_t dom) {
-  const uint4 x = philox(j, r, dom, 0u, key);
-  const float2 a = box_muller(x.x, x.y);
-  const float2 b = box_muller(x.z, x.w);
-  return make_float4(a.x, a.y, b.x, b.y);
+  return box_muller_x2(philox(j, r, dom, 0u, key));
 }
 
 // The four uniform entries (r, 4j .. 4j+3).
