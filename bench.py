@@ -116,18 +116,21 @@ class ClockSampler:
 
 def left_kernel_source_sha() -> str | None:
     """Hash of the left sketch's device code (constants, split pass, worker,
-    epilogue and MMA code of sk_tc.cu up to the right sketch), which the
-    committed ncu summary records; an edit elsewhere does not invalidate it."""
+    epilogue and MMA code of sk_tc.cu up to the right sketch, the PTX helpers
+    of sk_tc.cuh and the generator of sk_rng.cuh), which the committed ncu
+    summary records; an edit elsewhere does not invalidate it."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2603_20966_gb300", "csrc", "sk_tc.cu")
+    csrc = os.path.join(ROOT, "paper_2603_20966_gb300", "csrc")
     try:
-        text = open(src).read()
+        text = open(os.path.join(csrc, "sk_tc.cu")).read()
+        helpers = open(os.path.join(csrc, "sk_tc.cuh")).read()
+        rng = open(os.path.join(csrc, "sk_rng.cuh")).read()
     except OSError:
         return None
     i0, i1 = text.find("constexpr int BM = 128;"), text.find("// Right sketch Y[m x k]")
     if i0 < 0 or i1 < 0:
         return None
-    return hashlib.sha256(text[i0:i1].encode()).hexdigest()[:16]
+    return hashlib.sha256((text[i0:i1] + helpers + rng).encode()).hexdigest()[:16]
 
 
 def measured_traffic(dist: int):
