@@ -3,7 +3,9 @@ the CPU oracle would take hours: the reference is an FP64 product on the GPU
 (cuBLAS DGEMM through torch) of A with S materialized by the library in
 chunks.  sk_materialize is itself pinned bit-exact against the oracle
 (test_gpu_generator.py), and these references are cross-checked against the
-CPU oracle on sampled rows / columns in test_gpu_tc.py."""
+CPU oracle on sampled rows / columns in test_gpu_tc.py.  Covers the C2 left
+sketch (both distributions), the C3 right sketch, every member of the C4
+batch, and the C3 sketch used as a randomized range finder."""
 import numpy as np
 import pytest
 import torch
@@ -79,3 +81,77 @@ def test_c3_right_full_size(P):
         assert err <= TOL
     finally:
         P.sk_destroy(h)
+
+
+def test_c4_batch_every_member(P):
+    # the 256-problem batch exactly as bench.py builds and times it (tuned,
+    # graph-replayed on a created stream); every member against its FP64 product
+    from paper_2603_20966_gb300.workloads import batched_problems, gaussian_matrix
+    probs = batched_problems(256, seed=1000)
+    stream = torch.cuda.Stream()
+    b = P.sk_batch_create()
+    data = []
+    try:
+        for i, pr in enumerate(probs):
+            lda = (pr.n + 3) // 4 * 4
+            A = torch.zeros((pr.m, lda), device="cuda")
+            A[:, :pr.n] = gaussian_matrix(pr.m, pr.n, 5000 + i, device="cuda")
+            Y = torch.full((pr.k, lda), float("nan"), device="cuda")
+            h = P.sk_create(pr.seed, pr.dist, pr.k)
+            data.append((pr, h, A, Y))
+            P.sk_set_precision(h, 1)
+            P.sk_batch_add(b, h, A, pr.m, pr.n, lda, Y, lda)
+        torch.cuda.synchronize()
+        P.sk_batch_tune(b, stream)
+        P.sk_batch_run(b, stream)
+        assert P.sk_batch_status(b, stream) == 0
+        torch.cuda.synchronize()
+        worst = 0.0
+        for pr, h, A, Y in data:
+            S = _materialize(P, h, 0, 0, pr.k, pr.m, 1)
+            ref = P.sk_get_info(h)["scale"] * (S @ A[:, :pr.n].double())
+            err = _rel(Y[:, :pr.n], ref)
+            worst = max(worst, err)
+            assert err <= TOL, (pr, err)
+        print(f"C4 batch, 256 members: worst relative Frobenius error {worst:.3e}")
+    finally:
+        P.sk_batch_destroy(b)
+        for _, h, _, _ in data:
+            P.sk_destroy(h)
+
+
+def test_c3_range_finder(P):
+    # Q = orth(A Omega) for A = U V^T + 1e-3 E (rank 64, k = 256): the
+    # residual ||(I - Q Q^T) A||_F is the part of the noise outside range(Q):
+    # at most 1e-3 ||E||_F, and above it by no more than the factor
+    # sqrt(1 + 64 / (192 - 1)) of the randomized range finder's Frobenius
+    # bound with oversampling 192 (Halko, Martinsson and Tropp 2011, Thm 10.5)
+    from paper_2603_20966_gb300.workloads import gaussian_matrix, lowrank_plus_noise
+    m, n, k = 65536, 16384, 256
+    E = gaussian_matrix(m, n, 13, device="cuda")
+    noise = 1e-3 * torch.linalg.norm(E.double()).item()
+    del E
+    A = lowrank_plus_noise(m, n, device="cuda")
+    h = P.sk_create(7, 0, k)
+    P.sk_set_precision(h, 1)
+    Y = torch.empty((m, k), device="cuda")
+    try:
+        P.sk_apply_right(h, A, m, n, n, Y, k)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    Q, _ = torch.linalg.qr(Y.double())
+    B = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+    step = 8192
+    for r0 in range(0, m, step):
+        B += Q[r0:r0 + step].T @ A[r0:r0 + step].double()
+    res2 = 0.0
+    a2 = 0.0
+    for r0 in range(0, m, step):
+        Ad = A[r0:r0 + step].double()
+        res2 += torch.sum((Ad - Q[r0:r0 + step] @ B) ** 2).item()
+        a2 += torch.sum(Ad ** 2).item()
+    ratio = (res2 / a2) ** 0.5
+    expected = noise / a2 ** 0.5
+    print(f"C3 range finder: residual {ratio:.4e} of ||A||, noise {expected:.4e}")
+    assert 0.9 * expected <= ratio <= (1 + 64 / 191) ** 0.5 * expected
