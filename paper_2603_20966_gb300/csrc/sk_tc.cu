@@ -17,25 +17,28 @@
 // A pair owns a 256 x NT tile of Y (NT <= 512 TMEM columns in each CTA) and
 // one contiguous range of the contracted dimension m (deterministic split-K):
 //   warp 0       TMA producer: one 4D box per stage brings this CTA's
-//                columns of the hi and lo tiles [16 rows of m] into the
+//                columns of the hi and lo tiles [32 rows of m] into the
 //                operand ring, MN-major with the 128-byte swizzle;
 //   warp 1       TMEM allocation (collective over the pair); in the even CTA
-//                the MMA issuer: per stage 2 passes (hi, lo) x NT/256
-//                tcgen05.mma kind::f16 (M=256, K=16) into the FP32
+//                the MMA issuer: per stage 2 K steps x 2 passes (hi, lo) x
+//                NT/256 tcgen05.mma kind::f16 (M=256, K=16) into the FP32
 //                accumulator, completion signalled to both CTAs;
-//   warps 2-9    epilogue: every CHAIN stages the accumulator is read out of
-//                this CTA's TMEM and added into its FP32 partial in global
-//                memory (store for the first chain, red.add after);
+//   warps 2-9    epilogue: at the end of every accumulation chain (2048
+//                rows of m; 4096 for Rademacher S) the accumulator is read
+//                out of this CTA's TMEM and added into its FP32 partial in
+//                global memory (store for the first chain, red.add after);
 //   warps 10-25  workers, in 4 groups that take turns on successive stages:
-//                generate this CTA's BF16 S tile [128 x 16] (Philox4x32-10 +
+//                generate this CTA's BF16 S tile [128 x 32] (Philox4x32-10 +
 //                Box-Muller, or sign bits) in the K-major no-swizzle layout,
 //                then pass the stage on to the MMA issuer once this CTA's
 //                hi / lo tile has landed.
 // With k <= 128 a single CTA (cta_group::1, M = 128) does the same alone.
 // The tensor core accumulates in FP32 without round-to-nearest on every
 // add, so its error grows with the chain length; restarting the TMEM chain
-// every CHAIN stages and summing chains with IEEE adds keeps Y within 1e-5
-// of the exact product at any m.  S never exists outside shared memory.
+// at a fixed length and summing chains with IEEE adds keeps Y within 1e-5
+// of the exact product at any m.  S never exists outside shared memory
+// (except in the stored-S mode, which reads a caller's S by TMA to measure
+// the generate-versus-read trade).
 // Every wait is bounded: on timeout the kernel records SK_ETIMEOUT and the
 // waiting site in the handle's status words, drains its own copies and MMAs
 // (again bounded) and frees TMEM; both CTAs reach the closing cluster barrier.
@@ -139,6 +142,7 @@ struct alignas(128) LeftProblem {
   int64_t chunk;    // contracted length per split (multiple of LK)
   int nt;           // output columns per tile: a multiple of 128 (pairs) or 64 up to 256, or 512
   int dist;         // sk_dist of S
+  int chain;        // stages per TMEM accumulation chain (a power of two, multiple of 8)
   PhiloxKey key;
 };
 
@@ -270,7 +274,8 @@ struct ItemGeo {
   PhiloxKey key;  // (likewise)
   int64_t p0, q0, lbeg, lend;
   int nsteps, nt, nmma, nh, bh, cols, dist;
-  int coff;  // stages by which this item's chain boundaries are shifted
+  int chain;  // stages per accumulation chain
+  int coff;   // stages by which this item's chain boundaries are shifted
 };
 
 template <bool PAIR>
@@ -295,7 +300,8 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
   // that the accumulator drains of concurrent pairs do not all reach L2 at
   // once; the shift is a function of the item alone, so the summation order
   // of a problem does not depend on what runs beside it.
-  g.coff = ((it.tp * 7 + it.z * 13 + it.tq * 5) & 7) * (CHAIN_L / 8);
+  g.chain = g.pr->chain;
+  g.coff = ((it.tp * 7 + it.z * 13 + it.tq * 5) & 7) * (g.chain / 8);
   return g;
 }
 
@@ -493,7 +499,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * HCHUNK_BYTES;
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
-          const int ph = (s + ig.coff) % CHAIN_L;
+          const int ph = (s + ig.coff) & (ig.chain - 1);
           const bool chain_start = s == 0 || ph == 0;
           // a new chain may start only after every epilogue has read the last one
           if (chain_start && gc > 0 && !mbar_wait(acc_empty, (gc - 1) & 1, ab, 0x25, gc)) {
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             }
           }
-          const bool chain_end = ph == CHAIN_L - 1 || s == ig.nsteps - 1;
+          const bool chain_end = ph == ig.chain - 1 || s == ig.nsteps - 1;
           if (PAIR) {  // operands and accumulator are both CTAs'
             mma_commit_pair_both(empty_o(so));
             if (chain_end) mma_commit_pair_both(acc_full);
@@ -562,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t P = ig.pr->P, Q = ig.pr->Q;
       float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * Q + ig.q0;
       const bool vec_ok = (Q % 4) == 0;
-      const int nchains = (ig.nsteps + ig.coff + CHAIN_L - 1) / CHAIN_L;
+      const int nchains = (ig.nsteps + ig.coff + ig.chain - 1) / ig.chain;
       for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
         const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
         if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
@@ -1730,6 +1736,12 @@ bool encode_stored_map(CUtensorMap* map, const void* S, int64_t k, int64_t m, in
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Stages per accumulation chain of the left sketch.  The error of the split-A
+// product grows linearly with the chain length (full C2 size, chains of
+// 2048 / 4096 rows: Rademacher 3.5e-6 / 5.5e-6, Gaussian 5.1e-6 / 9.5e-6), so
+// Rademacher sketches drain the accumulator half as often as the others.
+int left_chain_stages(int dist) { return dist == kRademacher ? 2 * CHAIN_L : CHAIN_L; }
+
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
                   float* part, uint64_t seed, int dist) {
   memset(pr, 0, sizeof(*pr));
@@ -1741,6 +1753,7 @@ bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const
   pr->chunk = pl.chunk;
   pr->nt = pl.nt;
   pr->dist = dist;
+  pr->chain = left_chain_stages(dist);
   pr->key = make_key(seed);
   return true;
 }
