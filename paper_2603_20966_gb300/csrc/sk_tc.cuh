@@ -218,10 +218,14 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
   return r;
 }
 // Arrive on an mbarrier given by its shared::cluster address (any CTA of the
-// cluster), with release semantics at cluster scope.
+// cluster) with the instruction's default semantics (release, CTA scope).
+// Every producer that signals the peer this way has first made its own
+// shared-memory writes visible to the tensor core (fence.proxy.async) or
+// ordered its TMEM reads (tcgen05.fence::before_thread_sync); a cluster-scope
+// release on top of that made each arrive wait for a cluster-wide flush,
+// which cost the worker warps 13-18 % of their time in the right sketch.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_cluster() {
   asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
