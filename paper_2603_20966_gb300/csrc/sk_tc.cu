@@ -81,7 +81,6 @@ constexpr int WARP_TMA = 0;
 constexpr int WARP_MMA = 1;
 constexpr int WARP_EPI0 = 2;
 constexpr int WARP_WORK0 = WARP_EPI0 + NUM_EPI_WARPS;
-constexpr int NWORK = 32 * NUM_WORK_WARPS;
 constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 
 // Epilogue transpose tile of one warp: 32 accumulator rows x 16 columns,
