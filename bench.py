@@ -264,7 +264,8 @@ def run_batch(args):
         data.append((h, A, Y))
         flops += 2.0 * pr.k * pr.m * pr.n
     torch.cuda.synchronize(dev)
-    chosen = P.sk_batch_tune(b, stream)
+    P.sk_batch_tune(b, stream)
+    chosen = P.sk_batch_config(b)
     for _ in range(args.warmup):
         P.sk_batch_run(b, stream)
     st = P.sk_batch_status(b, stream)
@@ -308,7 +309,7 @@ def run_batch(args):
             "config": {"workload": "C4 batch of 256 left sketches, m log-uniform [1024, 65536], "
                                    "n uniform [32, 512], k = 2n, mixed Gaussian/Rademacher",
                        "problems": 256, "useful_tflop_per_step": flops / 1e12,
-                       "item_stages": chosen, "form": "bf16x2",
+                       "autotuned": chosen, "form": "bf16x2",
                        "l2": "inputs larger than L2 (A total "
                              f"{sum(p.m * p.n for p in probs) * 4 / 2**30:.2f} GiB)",
                        "parallelism": f"replicas x{world}"},

@@ -16,7 +16,7 @@ from ._native import (SK_BF16X2, sk_batch_add, sk_batch_create, sk_batch_destroy
                       sk_set_precision, sk_set_workspace, sk_stream_status, sk_version,
                       sk_workspace_size, status_string)
 from ._native import (sk_apply_left_noalloc, sk_apply_left_stored, sk_apply_right_e4m3,
-                      sk_nystrom, sk_quantize_e4m3)
+                      sk_batch_config, sk_batch_set_config, sk_nystrom, sk_quantize_e4m3)
 from ._native import (sk_server_create, sk_server_destroy, sk_server_fetch, sk_server_poll,
                       sk_server_release, sk_server_reset_stats, sk_server_stats_get,
                       sk_server_submit, sk_server_wait)
@@ -32,5 +32,5 @@ __all__ = [
     "sk_server_submit", "sk_server_poll", "sk_server_wait", "sk_server_fetch",
     "sk_server_release", "sk_server_stats_get", "sk_server_reset_stats", "sk_server_destroy",
     "sk_quantize_e4m3", "sk_apply_right_e4m3", "sk_nystrom", "sk_apply_left_noalloc",
-    "sk_apply_left_stored",
+    "sk_apply_left_stored", "sk_batch_set_config", "sk_batch_config",
 ]

@@ -42,6 +42,8 @@ PROTOTYPES = {
     "sk_batch_add": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64]),
     "sk_batch_run": (_int, [_vp, _vp]),
     "sk_batch_tune": (_int, [_vp, _vp, _P(_i64)]),
+    "sk_batch_set_config": (_int, [_vp, _i64, ctypes.c_int32, ctypes.c_int32]),
+    "sk_batch_config": (_int, [_vp, _P(_i64), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "sk_batch_status": (_int, [_vp, _vp]),
     "sk_batch_size": (_int, [_vp, _P(_i64)]),
     "sk_batch_destroy": (_int, [_vp]),
@@ -259,6 +261,18 @@ def sk_batch_tune(b, stream=None) -> int:
     c = ctypes.c_int64()
     _check("sk_batch_tune", _lib.sk_batch_tune(b, _stream(stream), ctypes.byref(c)))
     return c.value
+
+
+def sk_batch_set_config(b, item_stages, tile_cols, ring_stages) -> None:
+    _check("sk_batch_set_config",
+           _lib.sk_batch_set_config(b, int(item_stages), int(tile_cols), int(ring_stages)))
+
+
+def sk_batch_config(b) -> dict:
+    t, c, r = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check("sk_batch_config",
+           _lib.sk_batch_config(b, ctypes.byref(t), ctypes.byref(c), ctypes.byref(r)))
+    return {"item_stages": t.value, "tile_cols": c.value, "ring_stages": r.value}
 
 
 def sk_batch_status(b, stream=None) -> int:

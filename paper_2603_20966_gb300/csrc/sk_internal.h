@@ -87,6 +87,14 @@ struct BatchMember {
   int64_t item_stages = 0;   // own work-item length in stages of 16 rows, or 0
   bool split_ready = false;  // ws already holds the BF16 split of A (A is not read)
 };
+// Decomposition of a batch: item length (16-row units of m), widest output
+// tile (512 or 256 columns) and operand ring (the 8-stage narrow ring applies
+// only when every tile has at most 256 columns).
+struct BatchShape {
+  int64_t item_stages = 512;
+  int max_nt = 512;
+  bool narrow = false;
+};
 // Device buffers one batch launch uses; grown on demand, owned by the caller.
 struct BatchArena {
   void* d_buf = nullptr;  // work list + reduce descriptors

@@ -89,10 +89,13 @@ constexpr int EPI_PITCH = 20;
 constexpr uint32_t EPI_TILE = 32 * EPI_PITCH * 4;
 
 // Per-CTA buffers of the left kernel.  A CTA of a pair holds NT/2 columns of
-// each split A tile.
-template <bool PAIR>
+// each split A tile.  NARROW (pairs only, batches whose tiles all have at most
+// 256 columns): half-width split A slots, so the operand ring is 8 stages
+// deep instead of 5.
+template <bool PAIR, bool NARROW = false>
 struct Cfg {
-  static constexpr int COLS = PAIR ? NT_MAX / 2 : NT_MAX;   // most A columns per CTA
+  static_assert(PAIR || !NARROW, "narrow rings are a pair configuration");
+  static constexpr int COLS = NARROW ? NT_MAX / 4 : PAIR ? NT_MAX / 2 : NT_MAX;  // most A columns per CTA
   // Worker groups take turns on successive stages.  A group that starts
   // stage s has finished stage s - NGROUPS, so waits never run more than one
   // barrier phase ahead (the parity test would alias) as long as
@@ -100,7 +103,7 @@ struct Cfg {
   static constexpr int NGROUPS = PAIR ? 4 : 2;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NSO = PAIR ? 5 : 2;                  // operand stages
+  static constexpr int NSO = NARROW ? 8 : PAIR ? 5 : 2;     // operand stages
   static constexpr uint32_t OPB = 2u * COLS * LK * 2u;      // hi and lo tiles of a stage
   static constexpr uint32_t OPS = BM * LK * 2;              // S tile: KSTEPS slabs of 16
   static constexpr uint32_t OFF_B = 0;
@@ -395,10 +398,10 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
 constexpr int kMixed = -1;
 constexpr int kStored = 3;
 
-template <int DIST, bool PAIR>
+template <int DIST, bool PAIR, bool NARROW = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_sketch_bf16x2_left(const LeftSched sc) {
-  using C = Cfg<PAIR>;
+  using C = Cfg<PAIR, NARROW>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -1457,12 +1460,13 @@ int num_sms_tc() {
   return sms;
 }
 
-template <int DIST, bool PAIR>
+template <int DIST, bool PAIR, bool NARROW = false>
 cudaError_t set_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST, PAIR>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<PAIR>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST, PAIR, NARROW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<PAIR, NARROW>::SMEM);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1539,12 +1543,14 @@ struct LeftPlan {
   int64_t steps;             // stages of one item
 };
 
-LeftPlan left_geometry(const GemmShape& s, bool pair) {
+// max_nt: the widest output tile (512 columns, two MMA instructions per K
+// step; or 256, one instruction, more tiles along n).
+LeftPlan left_geometry(const GemmShape& s, bool pair, int max_nt = NT_MAX) {
   LeftPlan pl;
   pl.pair = pair;
   // every CTA holds whole 64-column chunks of the split A
   const int64_t gran = pair ? 2 * HCHUNK : HCHUNK;
-  pl.nt = s.Q > 256 ? 512 : static_cast<int>((s.Q + gran - 1) / gran * gran);
+  pl.nt = s.Q > 256 && max_nt > 256 ? 512 : static_cast<int>(std::min<int64_t>((s.Q + gran - 1) / gran * gran, 256));
   pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
   pl.tiles_p = (s.P + (pair ? 2 * BM : BM) - 1) / (pair ? 2 * BM : BM);
   pl.splits = 1;
@@ -1680,14 +1686,15 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
   return sc;
 }
 
-template <int DIST, bool PAIR>
+template <int DIST, bool PAIR, bool NARROW = false>
 cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
-  cudaError_t e = set_smem_attr<DIST, PAIR>();
+  cudaError_t e = set_smem_attr<DIST, PAIR, NARROW>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   fill_config<PAIR>(&cfg, attr, dim3(static_cast<unsigned>(units * (PAIR ? 2 : 1)), 1, 1), st);
-  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR>, sc);
+  cfg.dynamicSmemBytes = Cfg<PAIR, NARROW>::SMEM;
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR, NARROW>, sc);
 }
 
 template <bool PAIR>
@@ -2136,16 +2143,17 @@ struct PlannedBatch {
   int64_t max_elems = 0;
   int64_t units = 0;
   int launches = 0;                // kernels of one run: split (if any), sketch, reduce
+  bool narrow = false;             // launched with the 8-stage narrow ring
 };
 
-LeftPlan member_plan(const BatchMember& mb, int64_t item_stages, GemmShape* shape) {
-  if (mb.item_stages > 0) item_stages = mb.item_stages;
+LeftPlan member_plan(const BatchMember& mb, const BatchShape& bs, GemmShape* shape) {
+  const int64_t item_stages = mb.item_stages > 0 ? mb.item_stages : bs.item_stages;
   GemmShape s;
   s.left = true;
   s.P = mb.k;
   s.Q = mb.n;
   s.L = mb.m;
-  LeftPlan pl = left_geometry(s, true);
+  LeftPlan pl = left_geometry(s, true, bs.max_nt);
   const int64_t rows16 = (s.L + 15) / 16;  // item lengths count 16-row units
   set_splits(&pl, s, (rows16 + item_stages - 1) / item_stages);
   if (shape) *shape = s;
@@ -2159,15 +2167,17 @@ size_t partial_bytes(const LeftPlan& pl, const GemmShape& s) {
 // Work list of a batch whose arena workspace starts at `arena`; with `arena`
 // null only the arena size (`ws_bytes`) is computed.  A member's workspace
 // holds its BF16 split of A (split_bytes), then its partials.
-bool plan_members(const BatchMember* mbs, size_t count, int64_t item_stages, uint8_t* arena,
+bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, uint8_t* arena,
                   PlannedBatch* pb) {
   std::vector<LeftPlan> plans;
   std::vector<GemmShape> shapes;
   std::vector<size_t> ws_off;
   size_t total = 0;
+  pb->narrow = bs.narrow;
   for (size_t i = 0; i < count; ++i) {
     GemmShape s;
-    plans.push_back(member_plan(mbs[i], item_stages, &s));
+    plans.push_back(member_plan(mbs[i], bs, &s));
+    if (plans.back().nt > 256) pb->narrow = false;  // a wide tile needs the wide ring
     shapes.push_back(s);
     ws_off.push_back(total);  // 256-byte aligned: partials take 16-byte vector stores
     if (mbs[i].ws == nullptr) total += split_bytes(s.L, s.Q) + partial_bytes(plans.back(), s);
@@ -2225,12 +2235,12 @@ bool plan_members(const BatchMember* mbs, size_t count, int64_t item_stages, uin
 
 // Plan the members twice: once for the size of the arena, once with the
 // arena's workspace in place.
-cudaError_t plan_into_arena(const BatchMember* mbs, size_t count, int64_t item_stages,
+cudaError_t plan_into_arena(const BatchMember* mbs, size_t count, const BatchShape& bs,
                             BatchArena* ar, PlannedBatch* pb) {
-  if (!plan_members(mbs, count, item_stages, nullptr, pb)) return cudaErrorInvalidValue;
+  if (!plan_members(mbs, count, bs, nullptr, pb)) return cudaErrorInvalidValue;
   const cudaError_t e = grow_device(&ar->ws, &ar->ws_bytes, pb->ws_bytes + 256);
   if (e != cudaSuccess) return e;
-  if (!plan_members(mbs, count, item_stages, static_cast<uint8_t*>(ar->ws), pb))
+  if (!plan_members(mbs, count, bs, static_cast<uint8_t*>(ar->ws), pb))
     return cudaErrorInvalidValue;
   return cudaSuccess;
 }
@@ -2287,7 +2297,8 @@ cudaError_t launch_plan(const PlannedBatch& pb, const BatchArena& ar, cudaStream
     count_launches(1);
   }
   const LeftSched sc = device_sched(pb.hs, ar.d_buf, ar.d_status);
-  const cudaError_t e = launch_left<kMixed, true>(sc, pb.units, st);
+  const cudaError_t e = pb.narrow ? launch_left<kMixed, true, true>(sc, pb.units, st)
+                                  : launch_left<kMixed, true, false>(sc, pb.units, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
   return splitk_reduce_batched(reinterpret_cast<const ReduceDesc*>(b + pb.off_red),
@@ -2311,7 +2322,9 @@ int64_t spread_item_stages(const BatchMember& mb) {
 
 size_t batch_member_workspace(const BatchMember& mb, int64_t item_stages) {
   GemmShape s;
-  const LeftPlan pl = member_plan(mb, item_stages, &s);
+  BatchShape bs;
+  bs.item_stages = item_stages;
+  const LeftPlan pl = member_plan(mb, bs, &s);
   return split_bytes(s.L, s.Q) + partial_bytes(pl, s);
 }
 
@@ -2319,7 +2332,9 @@ cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t i
                                  BatchArena* ar, cudaEvent_t ready, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   PlannedBatch pb;
-  cudaError_t e = plan_into_arena(mbs, count, item_stages, ar, &pb);
+  BatchShape bs;
+  bs.item_stages = item_stages;
+  cudaError_t e = plan_into_arena(mbs, count, bs, ar, &pb);
   if (e == cudaSuccess) e = upload_plan(pb, ar, st);
   if (e == cudaSuccess && ready) e = cudaStreamWaitEvent(st, ready, 0);
   if (e == cudaSuccess) e = launch_plan(pb, *ar, st);
@@ -2334,7 +2349,8 @@ cudaError_t batch_launch_members(const BatchMember* mbs, size_t count, int64_t i
 struct sk_batch {
   std::vector<sk::BatchMember> entries;
   int device = 0;
-  int64_t item_stages = 0;  // tuned item length (stages); 0 = not chosen
+  sk::BatchShape shape;     // item length, tile width and ring of the next plan
+  bool chosen = false;      // shape set by sk_batch_tune or sk_batch_set_config
   bool planned = false;
   sk::BatchArena arena;     // work list, reduce descriptors, partials, status
   sk::PlannedBatch plan;
@@ -2343,7 +2359,6 @@ struct sk_batch {
 
 namespace {
 
-constexpr int64_t kDefaultItemStages = 512;
 
 std::string batch_signature(const sk_batch* b) {
   std::string sig;
@@ -2357,6 +2372,22 @@ std::string batch_signature(const sk_batch* b) {
   for (unsigned char c : sig) hsh = (hsh ^ c) * 1099511628211ull;
   snprintf(buf, sizeof(buf), "%016llx", static_cast<unsigned long long>(hsh));
   return std::string(buf);
+}
+
+// A tuned shape as one integer of the cache file: item stages in the low 20
+// bits, bit 20 = 256-column tiles, bit 21 = narrow ring.
+int64_t encode_shape(const sk::BatchShape& bs) {
+  return bs.item_stages | (bs.max_nt <= 256 ? (int64_t(1) << 20) : 0) |
+         (bs.narrow ? (int64_t(1) << 21) : 0);
+}
+
+bool decode_shape(int64_t v, sk::BatchShape* bs) {
+  const int64_t stages = v & ((int64_t(1) << 20) - 1);
+  if (stages <= 0 || (v >> 22) != 0) return false;
+  bs->item_stages = stages;
+  bs->max_nt = (v >> 20) & 1 ? 256 : 512;
+  bs->narrow = ((v >> 21) & 1) != 0;
+  return true;
 }
 
 int64_t cache_lookup(const std::string& sig) {
@@ -2410,10 +2441,10 @@ void batch_invalidate(sk_batch* b) {
 
 sk_status to_status(cudaError_t e) { return sk::status_from_cuda(e); }
 
-// Plan every member with items of about `item_stages` stages of 16 rows.
-sk_status batch_plan(sk_batch* b, int64_t item_stages, cudaStream_t st) {
-  cudaError_t e = sk::plan_into_arena(b->entries.data(), b->entries.size(), item_stages,
-                                      &b->arena, &b->plan);
+// Plan every member with items of about `bs.item_stages` stages of 16 rows.
+sk_status batch_plan(sk_batch* b, const sk::BatchShape& bs, cudaStream_t st) {
+  cudaError_t e = sk::plan_into_arena(b->entries.data(), b->entries.size(), bs, &b->arena,
+                                      &b->plan);
   if (e == cudaErrorInvalidValue) return SK_EINVAL;
   if (e == cudaSuccess) e = sk::upload_plan(b->plan, &b->arena, st);
   if (e != cudaSuccess) return to_status(e);
@@ -2496,10 +2527,9 @@ sk_status sk_batch_run(sk_batch_handle b, void* stream) {
   if (!b || b->entries.empty()) return SK_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!b->planned) {
-    int64_t t = b->item_stages;
-    if (t <= 0) t = cache_lookup(batch_signature(b));
-    if (t <= 0) t = kDefaultItemStages;
-    const sk_status ps = batch_plan(b, t, st);
+    sk::BatchShape bs = b->shape;
+    if (!b->chosen && !decode_shape(cache_lookup(batch_signature(b)), &bs)) bs = sk::BatchShape();
+    const sk_status ps = batch_plan(b, bs, st);
     if (ps != SK_OK) return ps;
   }
   return batch_run_once(b, st, true);
@@ -2508,16 +2538,30 @@ sk_status sk_batch_run(sk_batch_handle b, void* stream) {
 sk_status sk_batch_tune(sk_batch_handle b, void* stream, int64_t* chosen) {
   if (!b || b->entries.empty()) return SK_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t cands[] = {128, 256, 512, 1024, 2048, 4096};
+  // tile width x operand ring x item length; the 512-column tiles only when
+  // some member is wider than 256 columns
+  bool wide = false;
+  for (const auto& e : b->entries) wide = wide || e.n > 256;
+  std::vector<sk::BatchShape> cands;
+  const int64_t lens[] = {128, 256, 512, 1024, 2048, 4096};
+  for (int variant = wide ? 0 : 1; variant < 3; ++variant) {
+    for (int64_t t : lens) {
+      sk::BatchShape bs;
+      bs.item_stages = t;
+      bs.max_nt = variant == 0 ? 512 : 256;
+      bs.narrow = variant == 2;
+      cands.push_back(bs);
+    }
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return to_status(cudaGetLastError());
   float best_ms = 1e30f;
-  int64_t best = kDefaultItemStages;
+  sk::BatchShape best;
   sk_status rs = SK_OK;
-  for (int64_t t : cands) {
+  for (const auto& bs : cands) {
     batch_invalidate(b);
-    rs = batch_plan(b, t, st);
+    rs = batch_plan(b, bs, st);
     if (rs != SK_OK) break;
     rs = batch_run_once(b, st, false);  // warm-up
     if (rs != SK_OK) break;
@@ -2529,16 +2573,42 @@ sk_status sk_batch_tune(sk_batch_handle b, void* stream, int64_t* chosen) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = t;
+      best = bs;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   batch_invalidate(b);
   if (rs != SK_OK) return rs;
-  b->item_stages = best;
-  cache_store(batch_signature(b), best);
-  if (chosen) *chosen = best;
+  b->shape = best;
+  b->chosen = true;
+  cache_store(batch_signature(b), encode_shape(best));
+  if (chosen) *chosen = best.item_stages;
+  return SK_OK;
+}
+
+sk_status sk_batch_set_config(sk_batch_handle b, int64_t item_stages, int32_t tile_cols,
+                              int32_t ring_stages) {
+  if (!b || item_stages < 1 || item_stages >= (int64_t(1) << 20)) return SK_EINVAL;
+  if (tile_cols != 256 && tile_cols != 512) return SK_EINVAL;
+  if (ring_stages != 5 && ring_stages != 8) return SK_EINVAL;
+  if (ring_stages == 8 && tile_cols != 256) return SK_EINVAL;
+  batch_invalidate(b);
+  b->shape.item_stages = item_stages;
+  b->shape.max_nt = tile_cols;
+  b->shape.narrow = ring_stages == 8;
+  b->chosen = true;
+  return SK_OK;
+}
+
+sk_status sk_batch_config(sk_batch_handle b, int64_t* item_stages, int32_t* tile_cols,
+                          int32_t* ring_stages) {
+  if (!b) return SK_EINVAL;
+  sk::BatchShape bs = b->shape;
+  if (!b->chosen && !decode_shape(cache_lookup(batch_signature(b)), &bs)) bs = sk::BatchShape();
+  if (item_stages) *item_stages = bs.item_stages;
+  if (tile_cols) *tile_cols = bs.max_nt;
+  if (ring_stages) *ring_stages = bs.narrow ? 8 : 5;
   return SK_OK;
 }
 

@@ -114,12 +114,63 @@ def test_batch_agrees_with_single_calls(P):
         _free(P, data, b)
 
 
+# (item stages, tile columns, ring stages): the kernel configurations the
+# autotuner chooses from
+CONFIGS = [(512, 512, 5), (256, 256, 5), (1024, 256, 8)]
+
+
+def _batch_cfg(P, data, cfg):
+    b = P.sk_batch_create()
+    for d in data:
+        P.sk_batch_add(b, d["h"], d["A"], d["m"], d["n"], d["lda"], d["Y"], d["lda"])
+    P.sk_batch_set_config(b, *cfg)
+    assert P.sk_batch_config(b) == dict(zip(("item_stages", "tile_cols", "ring_stages"), cfg))
+    P.sk_batch_run(b, _stream())
+    assert P.sk_batch_status(b, _stream()) == 0
+    return b
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_every_configuration_matches_oracle(P, orc, cfg):
+    data = _make(P, PROBS)
+    b = _batch_cfg(P, data, cfg)
+    try:
+        for d in data:
+            A = d["A"][:, :d["n"]].cpu().numpy()
+            ref = orc.apply_left(d["seed"], d["dist"], BF16, d["k"], A)
+            assert rel_frob(d["Y"][:, :d["n"]].cpu().numpy(), ref) <= TOL, (cfg, d["n"])
+        mix = [d["Y"][:, :d["n"]].clone() for d in data]
+    finally:
+        _free(P, data, b)
+    # the same configuration alone gives the same bits
+    for i in (1, 2):
+        alone = _make(P, [PROBS[i]], seeds_a=7 + i)
+        b1 = _batch_cfg(P, alone, cfg)
+        assert torch.equal(alone[0]["Y"][:, :alone[0]["n"]], mix[i]), (cfg, i)
+        _free(P, alone, b1)
+
+
+def test_set_config_rejects_bad_values(P):
+    b = P.sk_batch_create()
+    try:
+        for bad in [(0, 512, 5), (512, 384, 5), (512, 512, 6), (512, 512, 8)]:
+            with pytest.raises(P.SketchError):
+                P.sk_batch_set_config(b, *bad)
+        assert P.sk_batch_config(b) == {"item_stages": 512, "tile_cols": 512, "ring_stages": 5}
+    finally:
+        P.sk_batch_destroy(b)
+
+
 def test_autotune_then_correct(P, orc, tmp_path, monkeypatch):
     monkeypatch.setenv("SK_TUNE_CACHE", str(tmp_path / "tune.json"))
     data = _make(P, PROBS[:5])
     b, chosen = _batch(P, data, tune=True)
     try:
         assert chosen in (128, 256, 512, 1024, 2048, 4096)
+        cfg = P.sk_batch_config(b)
+        assert cfg["item_stages"] == chosen
+        assert cfg["tile_cols"] in (256, 512) and cfg["ring_stages"] in (5, 8)
+        assert cfg["ring_stages"] == 5 or cfg["tile_cols"] == 256
         assert (tmp_path / "tune.json").exists()
         for d in data:
             A = d["A"][:, :d["n"]].cpu().numpy()
