@@ -226,10 +226,10 @@ sk_status sk_stream_status(sk_handle h, void* stream);
  *
  * A batch collects left sketches Y_i = S_i A_i (each with its own handle,
  * hence its own seed, distribution and k, and its own m, n) and runs them in
- * one launch of the persistent tensor-core kernel: CTA pairs walk
- * per-pair lists of (problem, tile, split) work items built on the host
- * (longest items first, each to the least-loaded pair), then one launch
- * reduces every problem's split partials in fixed order.  The two launches
+ * one launch of the persistent tensor-core kernel: the (problem, tile,
+ * split) work items, ordered longest first on the host, are handed out on
+ * the device by an atomic queue to whichever CTA pair is free; then one
+ * launch reduces every problem's split partials in fixed order.  The two launches
  * are captured once into a CUDA graph and replayed by later sk_batch_run
  * calls on an unchanged batch (on a created stream; on the legacy default
  * stream, which cannot be captured, the two launches are issued directly).  Each member's result is bit-identical to
@@ -402,7 +402,8 @@ sk_status sk_server_destroy(sk_server_handle s);
  * [1] where the first bounded wait that gave up was waiting (role * 16 +
  * barrier: roles 1 TMA producer, 2 MMA issuer, 3 epilogue, 4 worker;
  * barriers 0 staging full, 1 staging empty, 2 operand full, 3 operand empty,
- * 4 accumulator full, 5 accumulator empty), [2] the pipeline stage (or
+ * 4 accumulator full, 5 accumulator empty, 8 work-queue slot free, 9 work
+ * item published), [2] the pipeline stage (or
  * accumulation chain) it was waiting for, [3] the linear index of its CTA.
  * Words 1-3 are meaningful only when word 0 is SK_ETIMEOUT. */
 sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]);

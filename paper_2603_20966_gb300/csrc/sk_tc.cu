@@ -76,6 +76,7 @@ constexpr int CHAIN_L = CHAIN / KSTEPS;  // left stages per chain
 constexpr int HCHUNK = 64;    // columns of one 128-byte swizzle atom of the split A
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_WORK_WARPS = 16;
+constexpr int IQ = 4;  // slots of the left kernel's work-item queue in shared memory
 
 constexpr int WARP_TMA = 0;
 constexpr int WARP_MMA = 1;
@@ -110,9 +111,13 @@ struct Cfg {
   static constexpr uint32_t OFF_S = OFF_B + NSO * OPB;
   static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;    // epilogue transpose tiles
   static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
-  static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
-  static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
-  static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
+  static constexpr uint32_t NUM_BARS = 3 * NSO + 3 + 2 * IQ;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;  // abort flag, TMEM slot, item queue
+  static constexpr uint32_t SMEM = OFF_MISC + 16 + 4 * IQ + 1024;  // + slack for 1 KB alignment
+  // roles that read each queued item: in every CTA the epilogue and worker
+  // warps, plus the MMA issuer (even CTA) or the TMA producer (odd CTA); the
+  // even CTA's TMA producer fills the queue
+  static constexpr int IQ_READERS = (PAIR ? 2 : 1) * (1 + NUM_EPI_WARPS + NUM_WORK_WARPS);
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(NGROUPS <= NSO, "worker groups vs ring depth");
   static_assert(OPB % 1024 == 0, "split tiles start on swizzle-atom boundaries");
@@ -154,12 +159,14 @@ struct LeftItem {
   int prob, tp, tq, z;
 };
 
-// Work lists: the items of pair (or single CTA) i are
-// items[begin[i] .. begin[i+1]).
+// Work list: every item of the launch, longest first.  Pairs (or single
+// CTAs) take the next unclaimed item from the device counter `claim` (zero
+// at launch) until the list is exhausted.
 struct LeftSched {
   const LeftProblem* probs;
   const LeftItem* items;
-  const int* begin;
+  int* claim;
+  int nitems;
   int* status;
   uint64_t timeout_ns;
 };
@@ -423,9 +430,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? (cluster_ctarank() & 1u) : 0u;  // 0 = even (MMA issuer)
   const bool leader = rank == 0;
-  const int unit = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
-  const int ib = sc.begin[unit];
-  const int ie = sc.begin[unit + 1];
+  // item queue: slot i holds the index of the item every role of the pair
+  // (or single CTA) works on next; iq_full / iq_empty: written / read by all
+  int* iq = reinterpret_cast<int*>(smem + C::OFF_MISC + 16);
+  auto iq_full = [&](int i) { return bar0 + 8u * (3 * C::NSO + 3 + i); };
+  auto iq_empty = [&](int i) { return bar0 + 8u * (3 * C::NSO + 3 + IQ + i); };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NSO; ++i) {
@@ -436,6 +445,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_EPI_WARPS * (PAIR ? 2 : 1));  // epilogues of both CTAs
     mbar_init(drain_bar, 1);
+    for (int i = 0; i < IQ; ++i) {
+      mbar_init(iq_full(i), 1);
+      mbar_init(iq_empty(i), C::IQ_READERS);
+    }
     *abort_flag = 0;
     mbar_fence_init();
   }
@@ -458,11 +471,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t lead_full_o = PAIR ? mapa_shared(full_o(0), 0u) : full_o(0);
   const uint32_t lead_acc_empty = PAIR ? mapa_shared(acc_empty, 0u) : acc_empty;
 
+  // The even CTA's TMA producer claims item j of this pair and publishes it in
+  // both CTAs' queue slot (-1 once the list is exhausted).
+  auto produce_item = [&](int j) -> int {
+    const int slot = j % IQ;
+    if (j >= IQ && !mbar_wait(iq_empty(slot), ((j / IQ) & 1) ^ 1, ab, 0x18, j)) return -1;
+    int idx = atomicAdd(sc.claim, 1);
+    if (idx >= sc.nitems) idx = -1;
+    iq[slot] = idx;
+    mbar_arrive(iq_full(slot));
+    if (PAIR) {
+      st_shared_cluster(mapa_shared(smem_u32(iq + slot), 1u), idx);
+      mbar_arrive_release_cluster(mapa_shared(iq_full(slot), 1u));
+    }
+    return idx;
+  };
+  // Every other role reads item j from its own CTA's slot (one thread per
+  // role) and tells the producer the slot has been read.
+  auto read_item = [&](int j) -> int {
+    const int slot = j % IQ;
+    if (!mbar_wait<true>(iq_full(slot), (j / IQ) & 1, ab, 0x19, j)) return -1;
+    const int idx = *reinterpret_cast<volatile int*>(iq + slot);
+    if (PAIR && !leader)
+      mbar_arrive_cluster(mapa_shared(iq_empty(slot), 0u));
+    else
+      mbar_arrive(iq_empty(slot));
+    return idx;
+  };
+  auto read_item_warp = [&](int j) -> int {
+    int idx = -1;
+    if (lane == 0) idx = read_item(j);
+    return __shfl_sync(0xffffffffu, idx, 0);
+  };
+
   if (warp == WARP_TMA) {
     if (lane == 0) {
       int g = 0;
       int issued = 0;
-      for (int idx = ib; idx < ie && !*abort_flag; ++idx) {
+      for (int j = 0; !*abort_flag; ++j) {
+        const int idx = leader ? produce_item(j) : read_item(j);
+        if (idx < 0) break;
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const CUtensorMap* map = &ig.pr->map;
         tma_prefetch_desc(map);
@@ -493,7 +541,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0 && leader) {
       int g = 0, gc = 0;
       bool stop = false;
-      for (int idx = ib; idx < ie && !stop; ++idx) {
+      for (int j = 0; !stop; ++j) {
+        const int idx = read_item(j);
+        if (idx < 0) break;
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const uint32_t idesc =
             idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
@@ -564,7 +614,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
     int gc = 0;
     bool stop = false;
-    for (int idx = ib; idx < ie && !stop; ++idx) {
+    for (int j = 0; !stop; ++j) {
+      const int idx = read_item_warp(j);
+      if (idx < 0) break;
       const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
       const LeftItem it = sc.items[idx];
       const int64_t P = ig.pr->P, Q = ig.pr->Q;
@@ -653,7 +705,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint4 words[RAD_IT];
     int g = 0;
     bool stop = false;
-    for (int idx = ib; idx < ie && !stop; ++idx) {
+    for (int j = 0; !stop; ++j) {
+      const int idx = read_item_warp(j);
+      if (idx < 0) break;
       const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
 #pragma unroll
       for (int it = 0; it < RAD_IT; ++it) {  // Philox words belong to one problem and row
@@ -1620,14 +1674,18 @@ cudaError_t split_launch_one(const float* A, int64_t lda, int64_t m, int64_t n, 
 struct HostSched {
   std::vector<LeftProblem> probs;
   std::vector<LeftItem> items;
-  std::vector<int> begin;
-  size_t off_items = 0, off_begin = 0, bytes = 0;
+  int64_t units = 0;  // pairs (or CTAs) to launch
+  size_t off_items = 0, off_claim = 0, bytes = 0;
   std::vector<uint8_t> blob;
 };
 
-// Items of every problem, longest first, each to the least-loaded of at most
-// `max_units` units (pairs or CTAs).
-void build_items(const std::vector<LeftPlan>& plans, int64_t max_units, HostSched* hs) {
+// Items of every problem, longest (estimated) first; the kernel hands them
+// out in this order to whichever pair is free.  A stage costs about its
+// output columns plus a fixed 256 (generation, barriers), plus 640 for
+// Gaussian and uniform S (Box-Muller); launches use at most `max_units`
+// pairs (or CTAs).
+void build_items(const std::vector<LeftPlan>& plans, const std::vector<int>& dists,
+                 int64_t max_units, HostSched* hs) {
   struct Cand {
     LeftItem it;
     double cost;
@@ -1635,7 +1693,8 @@ void build_items(const std::vector<LeftPlan>& plans, int64_t max_units, HostSche
   std::vector<Cand> cands;
   for (size_t pi = 0; pi < plans.size(); ++pi) {
     const LeftPlan& pl = plans[pi];
-    const double cost = static_cast<double>(pl.steps) * (static_cast<double>(pl.nt) + 256.0);
+    const double gen = dists[pi] == kRademacher ? 0.0 : 640.0;
+    const double cost = static_cast<double>(pl.steps) * (static_cast<double>(pl.nt) + 256.0 + gen);
     for (int64_t z = 0; z < pl.splits; ++z)
       for (int64_t tq = 0; tq < pl.tiles_q; ++tq)
         for (int64_t tp = 0; tp < pl.tiles_p; ++tp)
@@ -1645,34 +1704,20 @@ void build_items(const std::vector<LeftPlan>& plans, int64_t max_units, HostSche
   }
   std::stable_sort(cands.begin(), cands.end(),
                    [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
-  const int64_t units = std::max<int64_t>(1, std::min<int64_t>(max_units, cands.size()));
-  std::vector<double> load(units, 0.0);
-  std::vector<std::vector<LeftItem>> per(units);
-  for (const Cand& c : cands) {
-    int64_t best = 0;
-    for (int64_t u = 1; u < units; ++u)
-      if (load[u] < load[best]) best = u;
-    load[best] += c.cost;
-    per[best].push_back(c.it);
-  }
   hs->items.clear();
-  hs->begin.assign(1, 0);
-  for (int64_t u = 0; u < units; ++u) {
-    for (const LeftItem& it : per[u]) hs->items.push_back(it);
-    hs->begin.push_back(static_cast<int>(hs->items.size()));
-  }
+  for (const Cand& c : cands) hs->items.push_back(c.it);
+  hs->units = std::max<int64_t>(1, std::min<int64_t>(max_units, cands.size()));
 }
 
 void pack_sched(HostSched* hs) {
   const size_t pb = hs->probs.size() * sizeof(LeftProblem);
   hs->off_items = (pb + 255) / 256 * 256;
   const size_t ib = hs->items.size() * sizeof(LeftItem);
-  hs->off_begin = (hs->off_items + ib + 255) / 256 * 256;
-  hs->bytes = hs->off_begin + hs->begin.size() * sizeof(int);
+  hs->off_claim = (hs->off_items + ib + 255) / 256 * 256;
+  hs->bytes = hs->off_claim + 256;
   hs->blob.assign(hs->bytes, 0);
   memcpy(hs->blob.data(), hs->probs.data(), pb);
   memcpy(hs->blob.data() + hs->off_items, hs->items.data(), ib);
-  memcpy(hs->blob.data() + hs->off_begin, hs->begin.data(), hs->begin.size() * sizeof(int));
 }
 
 LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
@@ -1680,7 +1725,8 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
   uint8_t* b = static_cast<uint8_t*>(dbuf);
   sc.probs = reinterpret_cast<const LeftProblem*>(b);
   sc.items = reinterpret_cast<const LeftItem*>(b + hs.off_items);
-  sc.begin = reinterpret_cast<const int*>(b + hs.off_begin);
+  sc.claim = reinterpret_cast<int*>(b + hs.off_claim);
+  sc.nitems = static_cast<int>(hs.items.size());
   sc.status = status;
   sc.timeout_ns = 2000000000ull;  // 2 s per wait: far beyond any healthy stage
   return sc;
@@ -1689,6 +1735,8 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
 template <int DIST, bool PAIR, bool NARROW = false>
 cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
   cudaError_t e = set_smem_attr<DIST, PAIR, NARROW>();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sc.claim, 0, sizeof(int), st);  // the work list starts unclaimed
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
@@ -2094,7 +2142,7 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
     return cudaErrorInvalidValue;
   if (S_stored && !encode_stored_map(&hs.probs[0].smap, S_stored, s.P, s.L, lds))
     return cudaErrorInvalidValue;
-  build_items(std::vector<LeftPlan>{pl}, units, &hs);
+  build_items(std::vector<LeftPlan>{pl}, std::vector<int>{h->dist}, units, &hs);
   pack_sched(&hs);
   if (memcmp(key, hm->sched_key, sizeof(key)) != 0 || hm->d_sched_bytes < hs.bytes) {
     cudaError_t e = grow_device(&hm->d_sched, &hm->d_sched_bytes, hs.bytes);
@@ -2104,7 +2152,7 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
     memcpy(hm->sched_key, key, sizeof(key));
   }
   const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status);
-  const int64_t nunits = static_cast<int64_t>(hs.begin.size()) - 1;
+  const int64_t nunits = hs.units;
   // the measurement hook brackets both passes: split of A, then the sketch
   prof_mark(h->prof_start, st);
   cudaError_t e = split_launch_one(A, lda, s.L, s.Q, H, st);
@@ -2221,9 +2269,11 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
   }
   const int64_t slots = pair_slots();
   if (slots <= 0) return false;
-  build_items(plans, slots / 2, &pb->hs);
+  std::vector<int> dists(count);
+  for (size_t i = 0; i < count; ++i) dists[i] = mbs[i].dist;
+  build_items(plans, dists, slots / 2, &pb->hs);
   pack_sched(&pb->hs);
-  pb->units = static_cast<int64_t>(pb->hs.begin.size()) - 1;
+  pb->units = pb->hs.units;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   pb->off_red = up(pb->hs.bytes);
   pb->off_split = up(pb->off_red + pb->red.size() * sizeof(ReduceDesc));

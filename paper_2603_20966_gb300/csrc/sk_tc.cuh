@@ -42,6 +42,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with acquire semantics at cluster scope: for data another CTA of
+// the cluster wrote into this CTA's shared memory before its arrive.
+__device__ __forceinline__ bool mbar_try_wait_acq_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], "
+      "%2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 
 // Shared abort state of one CTA: a flag every bounded wait polls, and the
 // device status word that records why the kernel gave up.
@@ -54,19 +66,25 @@ struct Abort {
 // Site codes recorded in status[1] by the first wait that gives up:
 // role * 16 + barrier, role 1 = TMA producer, 2 = MMA, 3 = epilogue,
 // 4 = worker; barrier 0 = staging full, 1 = staging empty, 2 = operand full,
-// 3 = operand empty, 4 = accumulator full, 5 = accumulator empty.
+// 3 = operand empty, 4 = accumulator full, 5 = accumulator empty, 8 = work
+// queue slot free, 9 = work item published (reported by the reading role's
+// first site code in use, 0x19).
 
 // Wait until the phase with `parity` of barrier `bar` completed.  Gives up
 // (returns false) when another thread of the CTA raised the abort flag or when
 // `limit_ns` elapsed, in which case it raises the flag and records
 // SK_ETIMEOUT (4) in the status word.
+template <bool CLUSTER_ACQUIRE = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const Abort& ab,
                                           int site = 0, int stage = 0) {
-  if (mbar_try_wait(bar, parity)) return true;
+  auto try_wait = [&]() {
+    return CLUSTER_ACQUIRE ? mbar_try_wait_acq_cluster(bar, parity) : mbar_try_wait(bar, parity);
+  };
+  if (try_wait()) return true;
   const uint64_t t0 = globaltimer();
   uint32_t it = 0;
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (try_wait()) return true;
     if ((++it & 63u) == 0) {
       if (*ab.flag) return false;
       if (globaltimer() - t0 > ab.limit_ns) {
@@ -226,6 +244,16 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
 // which cost the worker warps 13-18 % of their time in the right sketch.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// Arrive with release semantics at cluster scope, after this thread's stores
+// into another CTA's shared memory that the waiting side reads.
+__device__ __forceinline__ void mbar_arrive_release_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+// 32-bit store into shared memory of a CTA of the cluster (shared::cluster address).
+__device__ __forceinline__ void st_shared_cluster(uint32_t cluster_addr, int v) {
+  asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_cluster() {
   asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
