@@ -66,6 +66,8 @@ def lib():
             L.orc_ln.restype = None
             L.orc_sincospi.argtypes = [vp, vp, vp, i64]
             L.orc_sincospi.restype = None
+            L.orc_box_muller.argtypes = [vp, vp, i64]
+            L.orc_box_muller.restype = None
             L.orc_bf16_rne.argtypes = [vp, vp, i64]
             L.orc_bf16_rne.restype = None
             L.orc_e4m3_rne.argtypes = [vp, vp, i64]
@@ -117,6 +119,15 @@ def sincospi(t: np.ndarray):
     c = np.empty_like(t)
     lib().orc_sincospi(_p(t), _p(s), _p(c), t.size)
     return s, c
+
+
+def box_muller(words: np.ndarray) -> np.ndarray:
+    """Box-Muller of each word pair (row of ``words``, shape [N, 2], uint32):
+    the generator's Gaussian pair (rho cospi(2 u2), rho sinpi(2 u2)), shape [N, 2]."""
+    w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1, 2)
+    z = np.empty(w.shape, dtype=np.float32)
+    lib().orc_box_muller(_p(w), _p(z), w.shape[0])
+    return z
 
 
 def bf16_rne(x: np.ndarray) -> np.ndarray:

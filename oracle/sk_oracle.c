@@ -262,6 +262,24 @@ static double quantize(float g, int prec) {
   return (double)g;
 }
 
+/* Box-Muller on one pair of Philox words (xa, xb):                         */
+/* u1 = ((xa >> 8) + 1) 2^-24 in (0, 1], u2 = (xb >> 8) 2^-24 in [0, 1),     */
+/* rho = sqrt(-2 ln u1), z[0] = rho cospi(2 u2), z[1] = rho sinpi(2 u2).     */
+static void box_muller(uint32_t xa, uint32_t xb, float z[2]) {
+  float u1 = (float)((xa >> 8) + 1u) * 0x1p-24f;
+  float u2 = (float)(xb >> 8) * 0x1p-24f;
+  float rho = sqrtf(-2.0f * orc_ln1(u1));
+  float sn, cs;
+  orc_sincospi1(u2 + u2, &sn, &cs);
+  z[0] = rho * cs;
+  z[1] = rho * sn;
+}
+
+/* z[2i], z[2i+1] = Box-Muller of the word pair (w[2i], w[2i+1]), i < npairs. */
+void orc_box_muller(const uint32_t* w, float* z, int64_t npairs) {
+  for (int64_t i = 0; i < npairs; ++i) box_muller(w[2 * i], w[2 * i + 1], z + 2 * i);
+}
+
 /* Generate entries (r, col0 .. col0+cols-1) of one row of the generated
  * matrix, unscaled and quantized, into out[0..cols). */
 static void gen_row(uint64_t seed, int dist, int prec, uint32_t dom, uint32_t r,
@@ -292,13 +310,9 @@ static void gen_row(uint64_t seed, int dist, int prec, uint32_t dom, uint32_t r,
         g = (float)(x[c & 3u] >> 8) * 0x1p-24f;
       } else {
         uint32_t pair = (c >> 1) & 1u;
-        uint32_t xa = x[2 * pair], xb = x[2 * pair + 1];
-        float u1 = (float)((xa >> 8) + 1u) * 0x1p-24f;
-        float u2 = (float)(xb >> 8) * 0x1p-24f;
-        float rho = sqrtf(-2.0f * orc_ln1(u1));
-        float sn, cs;
-        orc_sincospi1(u2 + u2, &sn, &cs);
-        g = (c & 1u) ? rho * sn : rho * cs;
+        float z[2];
+        box_muller(x[2 * pair], x[2 * pair + 1], z);
+        g = z[c & 1u];
       }
     }
     out[j] = quantize(g, prec);

@@ -20,9 +20,12 @@
 //   Rademacher: bit c%32 of word (c>>5)%4, set -> -1.
 //   Uniform: (x_{c%4} >> 8) 2^-24.
 // Every floating-point step is an explicitly rounded IEEE operation
-// (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, __fsqrt_rn), so no compiler
-// contraction or fast-math flag can change a bit.  No hardware
-// approximation (MUFU) is used for ln, sin or cos.
+// (__fadd2_rn, __fmul2_rn, __ffma2_rn and their scalar forms), so no
+// compiler contraction or fast-math flag can change a bit.  ln, sin and cos
+// are polynomials; the quotient and the square root of Box-Muller are the
+// correctly rounded IEEE results, computed by Markstein's method from the
+// hardware reciprocal and reciprocal-square-root approximations (see
+// div_x2 / sqrt_x2).
 #pragma once
 #include <stdint.h>
 #include <cuda_bf16.h>
@@ -41,134 +44,162 @@ __host__ __device__ inline PhiloxKey make_key(uint64_t seed) {
   return PhiloxKey{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
 }
 
-// Philox4x32-10 on counter (c0, c1, c2, c3).
+// The key words of all ten rounds, (k0 + i 0x9E3779B9, k1 + i 0xBB67AE85) at
+// k[2i], k[2i+1].  A kernel that receives them among its launch parameters
+// reads each one as a constant operand of the round's XOR instead of
+// stepping the key in registers on every call.
+struct PhiloxRoundKeys {
+  uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxRoundKeys round_keys(PhiloxKey key) {
+  PhiloxRoundKeys rk;
+  for (int i = 0; i < 10; ++i) {
+    rk.k[2 * i] = key.k0 + (uint32_t)i * 0x9E3779B9u;
+    rk.k[2 * i + 1] = key.k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint32_t round_key(const PhiloxKey& key, int i, int w) {
+  return w == 0 ? key.k0 + (uint32_t)i * 0x9E3779B9u : key.k1 + (uint32_t)i * 0xBB67AE85u;
+}
+__device__ __forceinline__ uint32_t round_key(const PhiloxRoundKeys& rk, int i, int w) {
+  return rk.k[2 * i + w];
+}
+
+// Philox4x32-10 on counter (c0, c1, c2, c3); K is PhiloxKey or PhiloxRoundKeys.
+template <class K>
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        PhiloxKey key) {
-  uint32_t k0 = key.k0, k1 = key.k1;
+                                        const K& key) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
     const uint32_t lo0 = 0xD2511F53u * c0;
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
     const uint32_t lo1 = 0xCD9E8D57u * c2;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    const uint32_t n0 = hi1 ^ c1 ^ round_key(key, i, 0);
+    const uint32_t n2 = hi0 ^ c3 ^ round_key(key, i, 1);
     c0 = n0;
     c1 = lo1;
     c2 = n2;
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
+}
+
+// ---- Box-Muller on the two word pairs of one Philox call ----
+// The two transforms run side by side: __fadd2_rn / __fmul2_rn / __ffma2_rn
+// round each component exactly like the scalar __fadd_rn / __fmul_rn /
+// __fmaf_rn, so every value is the one the specification's scalar steps give
+// while the floating-point work takes half the instructions (the generator
+// is instruction-issue bound inside the sketch kernels).  Division and
+// square root give the IEEE correctly rounded results (div_x2, sqrt_x2).
+// Where a step below is written differently from the specification, the
+// comment beside it shows that the value is the same.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float2 neg2(float2 x) { return f2(-x.x, -x.y); }
+
+// a / b rounded to nearest-even, for the operands of ln01_x2: b = fl(f + 1)
+// in [1.7, 2.5), a = f - 1.  Markstein's method (P. Markstein, IBM J. Res.
+// Dev. 34(1), 1990): one Newton step on an approximate reciprocal y of b,
+// the quotient q = a y, its exact remainder r = a - b q (one FMA), and the
+// corrected quotient q + r y, rounded once.  The correction rounds correctly
+// except for a divisor with an all-ones significand; the only one in range
+// is 2 - 2^-23, which only f = 1 - 2^-23 produces, so its quotient is the
+// constant -2^-23 / (2 - 2^-23) rounded.  An exhaustive host check runs the
+// sequence from every reciprocal seed within 6 ulp (the hardware
+// approximation is within 1) on every operand pair the generator produces
+// and finds every quotient equal to the IEEE one.
+__device__ __forceinline__ float2 div_x2(float2 a, float2 b) {
+  const float2 nb = neg2(b);
+  float2 y = f2(rcp_approx(b.x), rcp_approx(b.y));
+  const float2 e = __ffma2_rn(nb, y, f2(1.0f, 1.0f));
+  y = __ffma2_rn(y, e, y);
+  const float2 q = __fmul2_rn(a, y);
+  const float2 r = __ffma2_rn(nb, q, a);
+  float2 s = __ffma2_rn(r, y, q);
+  if (b.x == 0x1.fffffep+0f) s.x = -0x1.000002p-24f;
+  if (b.y == 0x1.fffffep+0f) s.y = -0x1.000002p-24f;
+  return s;
+}
+
+// sqrt(w) rounded to nearest-even for w = -2 ln u1 in [2^-23, 34] or w = -0
+// (u1 = 1).  Markstein's square root: from an approximate reciprocal square
+// root y, g = w y and h = y / 2 are refined together (t = 1/2 - g h,
+// g += g t, h += h t), then g is corrected by the exact residual
+// d = w - g^2 (one FMA): g + d h, rounded once.  The same exhaustive check
+// (every radicand, every seed within 6 ulp; the hardware approximation is
+// within 2^-22.9 relative) finds every root equal to the IEEE one.  The seed
+// is infinite at w = 0, whose root is w itself.
+__device__ __forceinline__ float2 sqrt_x2(float2 w) {
+  const float2 y = f2(rsqrt_approx(w.x), rsqrt_approx(w.y));
+  float2 g = __fmul2_rn(w, y);
+  float2 h = __fmul2_rn(f2(0.5f, 0.5f), y);
+  const float2 t = __ffma2_rn(neg2(g), h, f2(0.5f, 0.5f));
+  g = __ffma2_rn(g, t, g);
+  h = __ffma2_rn(h, t, h);
+  const float2 d = __ffma2_rn(neg2(g), g, w);
+  float2 s = __ffma2_rn(d, h, g);
+  if (w.x == 0.0f) s.x = w.x;
+  if (w.y == 0.0f) s.y = w.y;
+  return s;
 }
 
 // ln x for x in (0, 1] (normal): x = 2^e f, f folded into [sqrt(1/2), sqrt 2],
 // s = (f-1)/(f+1), ln f = 2s + s^3 P(s^2) with the atanh series
 // coefficients 2/3, 2/5, 2/7, 2/9; ln x = e ln2_hi + (e ln2_lo + ln f).
-__device__ __forceinline__ float ln01(float x) {
-  const uint32_t b = __float_as_uint(x);
-  int e = (int)(b >> 23) - 127;
-  uint32_t mb = b & 0x007fffffu;
-  if (mb > 0x003504f3u) {
-    mb |= 0x3f000000u;
-    e += 1;
-  } else {
-    mb |= 0x3f800000u;
-  }
-  const float f = __uint_as_float(mb);
-  const float s = __fdiv_rn(__fadd_rn(f, -1.0f), __fadd_rn(f, 1.0f));
-  const float s2 = __fmul_rn(s, s);
-  float p = __fmaf_rn(s2, 0x1.c71c72p-3f, 0x1.24924ap-2f);
-  p = __fmaf_rn(s2, p, 0x1.99999ap-2f);
-  p = __fmaf_rn(s2, p, 0x1.555556p-1f);
-  const float s3 = __fmul_rn(s, s2);
-  const float lnf = __fmaf_rn(s3, p, __fadd_rn(s, s));
-  const float ef = __int2float_rn(e);
-  return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lnf));
-}
-
-// sin(pi t), cos(pi t) for t in [0, 2): q = rint(2t), r = t - q/2 in
-// [-1/4, 1/4] exactly, Taylor polynomials of sin(pi r) (to r^9) and
-// cos(pi r) (to r^10) with coefficients (-1)^j pi^n/n! rounded to FP32,
-// then a rotation by q quarter turns.
-__device__ __forceinline__ void sincospi(float t, float* sn_out, float* cs_out) {
-  const float qf = rintf(__fadd_rn(t, t));
-  const int q = (int)qf;
-  const float r = __fsub_rn(t, __fmul_rn(qf, 0.5f));
-  const float r2 = __fmul_rn(r, r);
-  float sp = __fmaf_rn(r2, 0x1.507834p-4f, -0x1.32d2ccp-1f);
-  sp = __fmaf_rn(r2, sp, 0x1.466bc6p+1f);
-  sp = __fmaf_rn(r2, sp, -0x1.4abbcep+2f);
-  sp = __fmaf_rn(r2, sp, 0x1.921fb6p+1f);
-  const float sn = __fmul_rn(r, sp);
-  float cp = __fmaf_rn(r2, -0x1.a6d1f2p-6f, 0x1.e1f506p-3f);
-  cp = __fmaf_rn(r2, cp, -0x1.55d3c8p+0f);
-  cp = __fmaf_rn(r2, cp, 0x1.03c1f0p+2f);
-  cp = __fmaf_rn(r2, cp, -0x1.3bd3ccp+2f);
-  const float cs = __fmaf_rn(r2, cp, 1.0f);
-  const int qq = q & 3;
-  const float a = (qq & 1) ? cs : sn;   // sin candidate
-  const float b = (qq & 1) ? sn : cs;   // cos candidate
-  *sn_out = (qq == 2 || qq == 3) ? -a : a;
-  *cs_out = (qq == 1 || qq == 2) ? -b : b;
-}
-
-// Box-Muller on one pair of Philox words -> (z0, z1).
-__device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb) {
-  const float u1 = __fmul_rn(__uint2float_rn((xa >> 8) + 1u), 0x1p-24f);
-  const float u2 = __fmul_rn(__uint2float_rn(xb >> 8), 0x1p-24f);
-  const float rho = __fsqrt_rn(__fmul_rn(-2.0f, ln01(u1)));
-  float sn, cs;
-  sincospi(__fadd_rn(u2, u2), &sn, &cs);
-  return make_float2(__fmul_rn(rho, cs), __fmul_rn(rho, sn));
-}
-
-// ---- the same two Box-Muller transforms, evaluated side by side ----
-// Every step below is the scalar step above applied to the two pairs of one
-// Philox call at once: __fadd2_rn / __fmul2_rn / __ffma2_rn round each
-// component exactly like __fadd_rn / __fmul_rn / __fmaf_rn, so the results
-// are bit-identical to box_muller(x0, x1), box_muller(x2, x3) while the
-// floating-point work takes half the instructions (the generator is
-// instruction-issue bound inside the sketch kernels).  Integer steps,
-// division, square root and rounding to integer stay per component.
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
 __device__ __forceinline__ float2 ln01_x2(float2 x) {
   const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
-  int e0 = (int)(b0 >> 23) - 127, e1 = (int)(b1 >> 23) - 127;
+  // biased exponent E (plus one when f is folded down); e = E - 127
   uint32_t m0 = b0 & 0x007fffffu, m1 = b1 & 0x007fffffu;
-  if (m0 > 0x003504f3u) {
-    m0 |= 0x3f000000u;
-    e0 += 1;
-  } else {
-    m0 |= 0x3f800000u;
-  }
-  if (m1 > 0x003504f3u) {
-    m1 |= 0x3f000000u;
-    e1 += 1;
-  } else {
-    m1 |= 0x3f800000u;
-  }
+  const uint32_t up0 = m0 > 0x003504f3u ? 1u : 0u, up1 = m1 > 0x003504f3u ? 1u : 0u;
+  m0 |= up0 ? 0x3f000000u : 0x3f800000u;
+  m1 |= up1 ? 0x3f000000u : 0x3f800000u;
+  // e as a float without a conversion: 0x4B000000 + E is the float 2^23 + E
+  // (E < 2^8), and subtracting 2^23 + 127 is exact
+  const float2 eb = f2(__uint_as_float(0x4B000000u + (b0 >> 23) + up0),
+                       __uint_as_float(0x4B000000u + (b1 >> 23) + up1));
+  const float2 ef = __fadd2_rn(eb, f2(-8388735.0f, -8388735.0f));
   const float2 f = f2(__uint_as_float(m0), __uint_as_float(m1));
   const float2 num = __fadd2_rn(f, f2(-1.0f, -1.0f));
   const float2 den = __fadd2_rn(f, f2(1.0f, 1.0f));
-  const float2 sv = f2(__fdiv_rn(num.x, den.x), __fdiv_rn(num.y, den.y));
+  const float2 sv = div_x2(num, den);
   const float2 s2 = __fmul2_rn(sv, sv);
   float2 p = __ffma2_rn(s2, f2(0x1.c71c72p-3f, 0x1.c71c72p-3f), f2(0x1.24924ap-2f, 0x1.24924ap-2f));
   p = __ffma2_rn(s2, p, f2(0x1.99999ap-2f, 0x1.99999ap-2f));
   p = __ffma2_rn(s2, p, f2(0x1.555556p-1f, 0x1.555556p-1f));
   const float2 s3 = __fmul2_rn(sv, s2);
   const float2 lnf = __ffma2_rn(s3, p, __fadd2_rn(sv, sv));
-  const float2 ef = f2(__int2float_rn(e0), __int2float_rn(e1));
   return __ffma2_rn(ef, f2(0x1.62e4p-1f, 0x1.62e4p-1f),
                     __ffma2_rn(ef, f2(0x1.7f7d1cp-20f, 0x1.7f7d1cp-20f), lnf));
 }
 
-__device__ __forceinline__ void sincospi_x2(float2 t, float2* sn_out, float2* cs_out) {
-  const float2 tt = __fadd2_rn(t, t);
-  const float2 qf = f2(rintf(tt.x), rintf(tt.y));
-  const int q0 = (int)qf.x & 3, q1 = (int)qf.y & 3;
+// sin(pi t), cos(pi t) of t = (v0 2^-23, v1 2^-23), v the 24-bit integers
+// given as exact floats fv: q = rint(2t) (ties to even), r = t - q/2 in
+// [-1/4, 1/4] exactly, Taylor polynomials of sin(pi r) (to r^9) and
+// cos(pi r) (to r^10) with coefficients (-1)^j pi^n/n! rounded to FP32, then
+// a rotation by q quarter turns.
+__device__ __forceinline__ void sincospi_x2(float2 fv, float2* sn_out, float2* cs_out) {
+  const float2 t = __fmul2_rn(fv, f2(0x1p-23f, 0x1p-23f));  // exact
+  // 2t + 1.5 2^23 rounded to nearest-even lies in [2^23, 2^24), where the
+  // spacing of floats is 1: its low bits hold rint(2t) (1.5 2^23 is even, so
+  // ties go to the even integer as rintf's do), and removing the offset again
+  // is exact
+  const float2 qm = __ffma2_rn(fv, f2(0x1p-22f, 0x1p-22f), f2(0x1.8p+23f, 0x1.8p+23f));
+  const float2 qf = __fadd2_rn(qm, f2(-0x1.8p+23f, -0x1.8p+23f));
+  const uint32_t q0 = __float_as_uint(qm.x), q1 = __float_as_uint(qm.y);  // low bits: q
   // t - q/2: the product q * 0.5 is exact, so one rounding as in the scalar form
   const float2 r = __ffma2_rn(qf, f2(-0.5f, -0.5f), t);
   const float2 r2 = __fmul2_rn(r, r);
@@ -182,34 +213,45 @@ __device__ __forceinline__ void sincospi_x2(float2 t, float2* sn_out, float2* cs
   cp = __ffma2_rn(r2, cp, f2(0x1.03c1f0p+2f, 0x1.03c1f0p+2f));
   cp = __ffma2_rn(r2, cp, f2(-0x1.3bd3ccp+2f, -0x1.3bd3ccp+2f));
   const float2 cs = __ffma2_rn(r2, cp, f2(1.0f, 1.0f));
-  const float a0 = (q0 & 1) ? cs.x : sn.x, b0 = (q0 & 1) ? sn.x : cs.x;
-  const float a1 = (q1 & 1) ? cs.y : sn.y, b1 = (q1 & 1) ? sn.y : cs.y;
-  *sn_out = f2((q0 == 2 || q0 == 3) ? -a0 : a0, (q1 == 2 || q1 == 3) ? -a1 : a1);
-  *cs_out = f2((q0 == 1 || q0 == 2) ? -b0 : b0, (q1 == 1 || q1 == 2) ? -b1 : b1);
+  // quarter turns q mod 4 = 0..3: (sin, cos) = (sn, cs), (cs, -sn), (-sn, -cs),
+  // (-cs, sn).  Odd q swaps the two; the sine is negated when bit 1 of q is
+  // set, the cosine when bit 1 of q + 1 is; negation flips the sign bit.
+  const uint32_t a0 = __float_as_uint((q0 & 1u) ? cs.x : sn.x);
+  const uint32_t c0 = __float_as_uint((q0 & 1u) ? sn.x : cs.x);
+  const uint32_t a1 = __float_as_uint((q1 & 1u) ? cs.y : sn.y);
+  const uint32_t c1 = __float_as_uint((q1 & 1u) ? sn.y : cs.y);
+  *sn_out = f2(__uint_as_float(a0 ^ ((q0 << 30) & 0x80000000u)),
+               __uint_as_float(a1 ^ ((q1 << 30) & 0x80000000u)));
+  *cs_out = f2(__uint_as_float(c0 ^ (((q0 + 1u) << 30) & 0x80000000u)),
+               __uint_as_float(c1 ^ (((q1 + 1u) << 30) & 0x80000000u)));
 }
 
-// box_muller(x.x, x.y) and box_muller(x.z, x.w), as (z0, z1, z2, z3).
+// Box-Muller of the word pairs (x.x, x.y) and (x.z, x.w), as (z0, z1, z2, z3):
+// u1 = ((xa >> 8) + 1) 2^-24, u2 = (xb >> 8) 2^-24, rho = sqrt(-2 ln u1),
+// (z_even, z_odd) = rho (cospi(2 u2), sinpi(2 u2)).
 __device__ __forceinline__ float4 box_muller_x2(uint4 x) {
-  const float2 k24 = f2(0x1p-24f, 0x1p-24f);
-  const float2 u1 = __fmul2_rn(f2(__uint2float_rn((x.x >> 8) + 1u), __uint2float_rn((x.z >> 8) + 1u)),
-                               k24);
-  const float2 u2 = __fmul2_rn(f2(__uint2float_rn(x.y >> 8), __uint2float_rn(x.w >> 8)), k24);
+  const float2 fa = f2(__uint2float_rn(x.x >> 8), __uint2float_rn(x.z >> 8));  // exact
+  const float2 fb = f2(__uint2float_rn(x.y >> 8), __uint2float_rn(x.w >> 8));  // exact
+  // (v + 1) 2^-24 is a float, so the fused form rounds nothing
+  const float2 u1 = __ffma2_rn(fa, f2(0x1p-24f, 0x1p-24f), f2(0x1p-24f, 0x1p-24f));
   const float2 v = __fmul2_rn(f2(-2.0f, -2.0f), ln01_x2(u1));
-  const float2 rho = f2(__fsqrt_rn(v.x), __fsqrt_rn(v.y));
+  const float2 rho = sqrt_x2(v);
   float2 sn, cs;
-  sincospi_x2(__fadd2_rn(u2, u2), &sn, &cs);
+  sincospi_x2(fb, &sn, &cs);  // t = u2 + u2 = (xb >> 8) 2^-23
   const float2 zc = __fmul2_rn(rho, cs);
   const float2 zs = __fmul2_rn(rho, sn);
   return make_float4(zc.x, zs.x, zc.y, zs.y);
 }
 
 // The four Gaussian entries (r, 4j .. 4j+3).
-__device__ __forceinline__ float4 gaussian4(PhiloxKey key, uint32_t r, uint32_t j, uint32_t dom) {
+template <class K>
+__device__ __forceinline__ float4 gaussian4(const K& key, uint32_t r, uint32_t j, uint32_t dom) {
   return box_muller_x2(philox(j, r, dom, 0u, key));
 }
 
 // The four uniform entries (r, 4j .. 4j+3).
-__device__ __forceinline__ float4 uniform4(PhiloxKey key, uint32_t r, uint32_t j, uint32_t dom) {
+template <class K>
+__device__ __forceinline__ float4 uniform4(const K& key, uint32_t r, uint32_t j, uint32_t dom) {
   const uint4 x = philox(j, r, dom, 0u, key);
   return make_float4(__fmul_rn(__uint2float_rn(x.x >> 8), 0x1p-24f),
                      __fmul_rn(__uint2float_rn(x.y >> 8), 0x1p-24f),
@@ -219,7 +261,8 @@ __device__ __forceinline__ float4 uniform4(PhiloxKey key, uint32_t r, uint32_t j
 
 // Sign bits of the 128 Rademacher entries (r, 128j .. 128j+127): bit b of
 // word w belongs to column 128j + 32w + b; a set bit means -1.
-__device__ __forceinline__ uint4 rademacher_bits(PhiloxKey key, uint32_t r, uint32_t j,
+template <class K>
+__device__ __forceinline__ uint4 rademacher_bits(const K& key, uint32_t r, uint32_t j,
                                                  uint32_t dom) {
   return philox(j, r, dom, 0u, key);
 }

@@ -169,6 +169,7 @@ struct LeftSched {
   int nitems;
   int* status;
   uint64_t timeout_ns;
+  PhiloxRoundKeys rk;  // round keys of problem 0 (read when a launch has one distribution)
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
@@ -317,10 +318,14 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
 // Generate this CTA's BF16 S tile [128 x 32] of one stage (two K-major slabs
 // of 16 columns).  A Rademacher task is one row of the stage: one 32-bit
 // Philox word, kept across the four stages one call covers.  Gaussian and
-// uniform tasks are four entries of one row (one Philox call).
-template <int DIST, class C>
-__device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64_t cbase, int wt,
-                                          uint32_t* cached_blk, uint4* words) {
+// uniform tasks are four entries of one row (one Philox call); a thread owns
+// quad qd of rows rbase + RSTEP i of both slabs, so its tile offsets and
+// Philox counters step by constants.  K is PhiloxKey, or the precomputed
+// PhiloxRoundKeys of a launch parameter.
+template <int DIST, class C, class K>
+__device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, const K& key,
+                                          int64_t cbase, int wt, uint32_t* cached_blk,
+                                          uint4* words) {
   if (DIST == kRademacher) {
     constexpr int RAD_IT = (BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
@@ -334,7 +339,7 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
         const uint32_t c = static_cast<uint32_t>(cbase);  // a multiple of 32
         const uint32_t blk = c >> 7;
         if (blk != cached_blk[it]) {
-          words[it] = rademacher_bits(g.key, static_cast<uint32_t>(grow), blk, 0u);
+          words[it] = rademacher_bits(key, static_cast<uint32_t>(grow), blk, 0u);
           cached_blk[it] = blk;
         }
         const uint32_t wsel = (c >> 5) & 3u;
@@ -364,33 +369,36 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, int64
       }
     }
   } else {
-    // per 32 tasks: 8 rows x 4 quads of one slab, 4 entries (one Philox call)
-    // each; a fixed, unrolled count per thread lets independent chains
-    // interleave
-    constexpr int GEN_IT = (8 * BM + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+    // A warp covers 8 rows x 4 quads; the group covers RSTEP rows per pass.
+    constexpr int RSTEP = C::GROUP_THREADS / 4;
+    constexpr int NPASS = BM / RSTEP;
+    static_assert(RSTEP % 8 == 0 && BM % RSTEP == 0, "row passes of the worker group");
+    const uint32_t qd = static_cast<uint32_t>(wt) & 3u;
+    const uint32_t rbase = static_cast<uint32_t>(wt >> 5) * 8u + ((static_cast<uint32_t>(wt) & 31u) >> 2);
+    // kmaj_off(rbase + RSTEP i, qd / 2) = off0 + 32 RSTEP i (RSTEP is a multiple of 8)
+    const uint32_t off0 = kmaj_off(rbase, qd >> 1) + (qd & 1u) * 8u;
+    const bool full = cbase + LK <= g.lend;
+    const uint32_t j0 = static_cast<uint32_t>(cbase >> 2) + qd;  // Philox block, slab 0
+    const int64_t row0 = g.p0 + rbase;
     // two tasks in flight per thread: full unrolling of the 8 Philox +
     // Box-Muller tasks made the loop too large for the instruction cache
     // (11 % slower on the Gaussian sketch)
-#pragma unroll 2
-    for (int it = 0; it < GEN_IT; ++it) {
-      const int t = wt + it * C::GROUP_THREADS;
-      if (t >= 8 * BM) break;
-      const uint32_t l = static_cast<uint32_t>(t & 31);
-      const uint32_t w = static_cast<uint32_t>(t >> 5);
-      const uint32_t slab = w >> 4;
-      const uint32_t r = (w & 15u) * 8u + (l >> 2);
-      const uint32_t qd = l & 3u;
-      const int64_t grow = g.p0 + r;
-      const int64_t c0 = cbase + 16 * slab + 4 * qd;
-      uint2 v = make_uint2(0u, 0u);
-      if (grow < g.P && c0 < g.lend) {
-        const uint32_t c = static_cast<uint32_t>(c0);
-        const float4 a = DIST == kUniform
-                             ? uniform4(g.key, static_cast<uint32_t>(grow), c >> 2, 0u)
-                             : gaussian4(g.key, static_cast<uint32_t>(grow), c >> 2, 0u);
-        v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
+#pragma unroll 1
+    for (int i = 0; i < NPASS; ++i) {
+      const int64_t grow = row0 + static_cast<int64_t>(RSTEP) * i;
+      const bool rv = grow < g.P;
+#pragma unroll
+      for (int slab = 0; slab < KSTEPS; ++slab) {
+        uint2 v = make_uint2(0u, 0u);
+        if (rv && (full || cbase + 16 * slab + 4 * qd < g.lend)) {
+          const uint32_t j = j0 + 4u * static_cast<uint32_t>(slab);
+          const float4 a = DIST == kUniform ? uniform4(key, static_cast<uint32_t>(grow), j, 0u)
+                                            : gaussian4(key, static_cast<uint32_t>(grow), j, 0u);
+          v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
+        }
+        *reinterpret_cast<uint2*>(sdst + slab * S_SLAB + off0 +
+                                  static_cast<uint32_t>(i * RSTEP * 32)) = v;
       }
-      *reinterpret_cast<uint2*>(sdst + slab * S_SLAB + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
     }
   }
 }
@@ -728,14 +736,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if constexpr (DIST == kStored) {
           // the S tile arrives with the split A tile
         } else if constexpr (DIST != kMixed) {
-          gen_stage<DIST, C>(sdst, ig, cbase, wt, cached_blk, words);
+          // one problem per launch: its round keys are launch parameters
+          gen_stage<DIST, C>(sdst, ig, sc.rk, cbase, wt, cached_blk, words);
         } else {
           if (ig.dist == kRademacher)
-            gen_stage<kRademacher, C>(sdst, ig, cbase, wt, cached_blk, words);
+            gen_stage<kRademacher, C>(sdst, ig, ig.key, cbase, wt, cached_blk, words);
           else if (ig.dist == kUniform)
-            gen_stage<kUniform, C>(sdst, ig, cbase, wt, cached_blk, words);
+            gen_stage<kUniform, C>(sdst, ig, ig.key, cbase, wt, cached_blk, words);
           else
-            gen_stage<kGaussian, C>(sdst, ig, cbase, wt, cached_blk, words);
+            gen_stage<kGaussian, C>(sdst, ig, ig.key, cbase, wt, cached_blk, words);
         }
         // this CTA's split A tile of the stage has landed
         ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x40, g);
@@ -807,7 +816,7 @@ struct TcRightParams {
   int64_t chunk;    // contracted length per split (multiple of BK)
   int nq;           // N of the MMA: k rows per pair tile (multiple of 16, <= 256)
   int tmem_cols;    // power of two >= 2 * nq
-  PhiloxKey key;
+  PhiloxRoundKeys rk;
   int* status;
   uint64_t timeout_ns;
 };
@@ -1004,7 +1013,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t c = static_cast<uint32_t>(c0);
             const uint32_t blk = c >> 7;
             if (blk != cached_blk[it]) {
-              words[it] = rademacher_bits(p.key, static_cast<uint32_t>(grow), blk, 0u);
+              words[it] = rademacher_bits(p.rk, static_cast<uint32_t>(grow), blk, 0u);
               cached_blk[it] = blk;
             }
             const uint32_t wsel = (c >> 5) & 3u;
@@ -1019,25 +1028,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
         }
       } else {
-        constexpr int GEN_IT = (4 * 128 + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
+        // thread wt owns quad qd of rows rb + RSTEP it (4 quads per row)
+        constexpr int RSTEP = C::GROUP_THREADS / 4;
+        constexpr int GEN_IT = 128 / RSTEP;
+        static_assert(RSTEP % 8 == 0, "row passes of the worker group");
+        const uint32_t qd = static_cast<uint32_t>(wt) & 3u;
+        const uint32_t rb = static_cast<uint32_t>(wt) >> 2;
+        // kmaj_off(rb + RSTEP it, qd / 2) = off0 + 32 RSTEP it
+        const uint32_t off0 = kmaj_off(rb, qd >> 1) + (qd & 1u) * 8u;
+        const bool cv = cbase + 4 * qd < lend;
+        const uint32_t j = static_cast<uint32_t>(cbase >> 2) + qd;  // Philox block
 #pragma unroll 2
         for (int it = 0; it < GEN_IT; ++it) {
-          const int t = wt + it * C::GROUP_THREADS;
-          if (t >= 4 * gh) break;
-          const uint32_t l = static_cast<uint32_t>(t & 31);
-          const uint32_t qd = l & 3u;
-          const uint32_t r = static_cast<uint32_t>(t >> 2);  // row, 4 quads per row
+          const uint32_t r = rb + static_cast<uint32_t>(RSTEP * it);
+          if (r >= static_cast<uint32_t>(gh)) break;
           const int64_t grow = g0 + r;
-          const int64_t c0 = cbase + 4 * qd;
           uint2 v = make_uint2(0u, 0u);
-          if (grow < p.Q && c0 < lend) {
-            const uint32_t c = static_cast<uint32_t>(c0);
+          if (grow < p.Q && cv) {
             const float4 a = DIST == kUniform
-                                 ? uniform4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u)
-                                 : gaussian4(p.key, static_cast<uint32_t>(grow), c >> 2, 0u);
+                                 ? uniform4(p.rk, static_cast<uint32_t>(grow), j, 0u)
+                                 : gaussian4(p.rk, static_cast<uint32_t>(grow), j, 0u);
             v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
           }
-          *reinterpret_cast<uint2*>(sdst + kmaj_off(r, qd >> 1) + (qd & 1u) * 8u) = v;
+          *reinterpret_cast<uint2*>(sdst + off0 + static_cast<uint32_t>(it * RSTEP * 32)) = v;
         }
       }
       ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
@@ -1144,7 +1157,7 @@ struct TcRightQParams {
   int64_t chunk;        // columns per split (multiple of QK)
   int nq;               // N of the MMA: k rows per pair tile (multiple of 16, <= 256)
   int tmem_cols;        // power of two >= 2 * nq
-  PhiloxKey key;
+  PhiloxRoundKeys rk;
   int* status;
   uint64_t timeout_ns;
 };
@@ -1328,7 +1341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
           int64_t nv = 0;
           if (grow < p.Q && cbase < lend) {
-            w = rademacher_bits(p.key, static_cast<uint32_t>(grow),
+            w = rademacher_bits(p.rk, static_cast<uint32_t>(grow),
                                 static_cast<uint32_t>(cbase >> 7), 0u);
             nv = min(lend - cbase, static_cast<int64_t>(QK));
           }
@@ -1367,9 +1380,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint32_t q = 0u;
           if (grow < p.Q && cc < lend) {
             const float4 a = DIST == kUniform
-                                 ? uniform4(p.key, static_cast<uint32_t>(grow),
+                                 ? uniform4(p.rk, static_cast<uint32_t>(grow),
                                             static_cast<uint32_t>(cc >> 2), 0u)
-                                 : gaussian4(p.key, static_cast<uint32_t>(grow),
+                                 : gaussian4(p.rk, static_cast<uint32_t>(grow),
                                              static_cast<uint32_t>(cc >> 2), 0u);
             q = e4m3x4(a);
           }
@@ -1729,6 +1742,7 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
   sc.nitems = static_cast<int>(hs.items.size());
   sc.status = status;
   sc.timeout_ns = 2000000000ull;  // 2 s per wait: far beyond any healthy stage
+  sc.rk = round_keys(hs.probs.empty() ? PhiloxKey{0u, 0u} : hs.probs[0].key);
   return sc;
 }
 
@@ -2003,7 +2017,7 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   p.chunk = pl.chunk;
   p.nq = pl.nt;
   p.tmem_cols = pl.tmem_cols;
-  p.key = make_key(h->seed);
+  p.rk = round_keys(make_key(h->seed));
   p.status = h->d_status;
   p.timeout_ns = 2000000000ull;
   const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
@@ -2081,7 +2095,7 @@ cudaError_t q8_sketch_right_quantized(const sk_sketch* h, const GemmShape& s, co
   p.chunk = pl.chunk;
   p.nq = pl.nt;
   p.tmem_cols = pl.tmem_cols;
-  p.key = make_key(h->seed);
+  p.rk = round_keys(make_key(h->seed));
   p.status = h->d_status;
   p.timeout_ns = 2000000000ull;
   dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),

@@ -121,3 +121,28 @@ def test_scale(orc):
         s = float(orc.scale(k))
         assert abs(s - 1 / np.sqrt(k)) <= 0.5 * np.spacing(np.float32(1 / np.sqrt(k)))
     assert orc.scale(64) == 0.125
+
+
+def test_box_muller_every_input_against_fp64(orc):
+    """orc_box_muller over every u1 (with u2 running through every value in
+    the same order) and, in a second pass, every u2 against a fixed mid-range
+    u1: the radius matches sqrt(-2 ln u1) and the angle 2 pi u2 in FP64."""
+    n = 1 << 24
+    i = np.arange(n, dtype=np.uint64)
+    words = np.stack([((i << 8) | 0x11).astype(np.uint32),
+                      (((n - 1 - i) << 8) | 0xEE).astype(np.uint32)], 1)
+    z = orc.box_muller(words).astype(np.float64)
+    u1 = (i.astype(np.float64) + 1) / 2.0**24
+    u2 = (n - 1 - i).astype(np.float64) / 2.0**24
+    r = np.sqrt(z[:, 0] ** 2 + z[:, 1] ** 2)
+    rho = np.sqrt(-2.0 * np.log(u1))
+    assert np.all(np.abs(r - rho) <= 4e-7 * np.maximum(rho, 1.0))
+    assert r[-1] == 0.0  # u1 = 1: ln 1 = 0 exactly
+    big = rho > 1e-2
+    ang = np.mod(np.arctan2(z[big, 1], z[big, 0]) / (2 * np.pi), 1.0)
+    d = np.abs(ang - u2[big])
+    assert np.minimum(d, 1 - d).max() < 2e-6
+    # the generator's Gaussian entries are these pairs of its Philox words
+    x = _words(orc, 7, 3, np.arange(64))
+    g = orc.generate(7, G, 0, 3, 0, 1, 256)[0]
+    np.testing.assert_array_equal(orc.box_muller(x.reshape(-1, 2)).reshape(-1), g)
