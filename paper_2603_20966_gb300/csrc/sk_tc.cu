@@ -1071,16 +1071,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
-          const float h0 = __uint_as_float(hw[e] << 16);
-          const float h1 = __uint_as_float(hw[e] & 0xffff0000u);
-          lw[e] = pack_bf16x2(__fsub_rn(a[2 * e], h0), __fsub_rn(a[2 * e + 1], h1));
+          const float2 hv = f2(__uint_as_float(hw[e] << 16), __uint_as_float(hw[e] & 0xffff0000u));
+          // a - hi of both elements in one packed FMA (the product by -1 is
+          // exact, so each component is the rounded difference)
+          const float2 lv = __ffma2_rn(hv, f2(-1.0f, -1.0f), f2(a[2 * e], a[2 * e + 1]));
+          lw[e] = pack_bf16x2(lv.x, lv.y);
         }
         const uint32_t o = static_cast<uint32_t>(row >> 7) * (C::OPA / 2) +
                            kmaj_off(static_cast<uint32_t>(row & 127), static_cast<uint32_t>(hh));
         *reinterpret_cast<uint4*>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      fence_proxy_async_cluster();
+      // the S half and the A operands are in this CTA's own shared memory
+      fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive_cluster(lead_full_o + 8u * so);

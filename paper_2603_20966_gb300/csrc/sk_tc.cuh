@@ -255,9 +255,6 @@ __device__ __forceinline__ void mbar_arrive_release_cluster(uint32_t cluster_add
 __device__ __forceinline__ void st_shared_cluster(uint32_t cluster_addr, int v) {
   asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
-__device__ __forceinline__ void fence_proxy_async_cluster() {
-  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-}
 // All threads of all CTAs of the cluster (warp-aligned).
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
