@@ -191,8 +191,11 @@ sk_status sk_apply_left_noalloc(sk_handle h, const float* A, int64_t m, int64_t 
 /* The same two products with HOST buffers: A is copied to the device, the
  * sketch computed, and Y copied back before the call returns (the call
  * synchronises `stream`).  Pinned host memory gives full copy bandwidth;
- * pageable memory works.  Device staging memory is owned by the handle and
- * reused across calls.  Errors as above plus SK_ENOMEM. */
+ * pageable memory works.  A (or Y) whose leading dimension equals its row
+ * length, a multiple of 4, moves as one linear copy; other layouts as a
+ * pitched copy.  Only the n (or output) columns of each row are read (or
+ * written).  Device staging memory is owned by the handle and reused across
+ * calls.  Errors as above plus SK_ENOMEM. */
 sk_status sk_apply_left_host(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
                              float* Y, int64_t ldy, void* stream);
 sk_status sk_apply_right_host(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,

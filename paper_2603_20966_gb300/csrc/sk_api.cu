@@ -134,13 +134,22 @@ sk_status apply_host(sk_sketch* h, const float* A, int64_t m, int64_t n, int64_t
   st = grow(&h->stage_Y, &h->stage_Y_bytes, (size_t)yr * (size_t)ldy_d * sizeof(float));
   if (st != SK_OK) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpy2DAsync(h->stage_A, lda_d * sizeof(float), A, lda * sizeof(float),
-                                    n * sizeof(float), m, cudaMemcpyHostToDevice, cs);
+  // rows without padding on either side (leading dimension = row length, a
+  // multiple of 4) move as one linear copy of exactly the matrix's bytes
+  cudaError_t e =
+      lda == n && lda_d == n
+          ? cudaMemcpyAsync(h->stage_A, A, (size_t)m * (size_t)lda * sizeof(float),
+                            cudaMemcpyHostToDevice, cs)
+          : cudaMemcpy2DAsync(h->stage_A, lda_d * sizeof(float), A, lda * sizeof(float),
+                              n * sizeof(float), m, cudaMemcpyHostToDevice, cs);
   if (e != cudaSuccess) return from_cuda(e);
   st = apply(h, h->stage_A, m, n, lda_d, h->stage_Y, ldy_d, stream, left);
   if (st != SK_OK) return st;
-  e = cudaMemcpy2DAsync(Y, ldy * sizeof(float), h->stage_Y, ldy_d * sizeof(float),
-                        yc * sizeof(float), yr, cudaMemcpyDeviceToHost, cs);
+  e = ldy == yc && ldy_d == yc
+          ? cudaMemcpyAsync(Y, h->stage_Y, (size_t)yr * (size_t)ldy * sizeof(float),
+                            cudaMemcpyDeviceToHost, cs)
+          : cudaMemcpy2DAsync(Y, ldy * sizeof(float), h->stage_Y, ldy_d * sizeof(float),
+                              yc * sizeof(float), yr, cudaMemcpyDeviceToHost, cs);
   if (e != cudaSuccess) return from_cuda(e);
   return from_cuda(cudaStreamSynchronize(cs));
 }

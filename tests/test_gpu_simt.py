@@ -108,6 +108,32 @@ def test_deterministic_and_host_entry_point(P):
     np.testing.assert_array_equal(Yh, a)
 
 
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("side", ["left", "right"])
+def test_host_entry_points_unpadded_rows(P, side, form):
+    """Host buffers whose rows need no padding (n and the output width
+    multiples of 4) take the linear-copy path; the result is the device
+    path's bit for bit, and nothing outside Y is written."""
+    m, n, k = 3000, 64, 48
+    A = _A(m, n, 11)
+    h = P.sk_create(21, G, k)
+    try:
+        P.sk_set_precision(h, form)
+        yshape = (k, n) if side == "left" else (m, k)
+        Yd = torch.empty(yshape, dtype=torch.float32, device="cuda")
+        f = P.sk_apply_left if side == "left" else P.sk_apply_right
+        f(h, A.cuda(), m, n, n, Yd, yshape[1])
+        torch.cuda.synchronize()
+        Yh = np.full((yshape[0] * yshape[1] + 8,), np.nan, np.float32)
+        An = np.ascontiguousarray(A.numpy())
+        g = P.sk_apply_left_host if side == "left" else P.sk_apply_right_host
+        g(h, An.ctypes.data, m, n, n, Yh.ctypes.data, yshape[1])
+    finally:
+        P.sk_destroy(h)
+    np.testing.assert_array_equal(Yh[:-8].reshape(yshape), Yd.cpu().numpy())
+    assert np.isnan(Yh[-8:]).all()
+
+
 def test_transposition_identity(P):
     A = _A(300, 200, 9)
     right = run(P, "right", 4, R, 24, A)
