@@ -557,6 +557,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
         const uint32_t pstride = static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
         const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * HCHUNK_BYTES;
+        // A descriptor holds its operand's address / 16 in its low 14 bits.
+        // Every offset below is a multiple of 16 B and every operand lies
+        // below 256 KB, so adding offset / 16 to a base descriptor's low word
+        // gives exactly the descriptor of the offset operand; the issuer adds
+        // instead of rebuilding each descriptor.
+        const uint64_t a_base = smem_desc(sbase + C::OFF_S, LBO, SBO);
+        const uint64_t b_base = smem_desc_sw128(sbase + C::OFF_B, B_LBO, B_SBO);
+        const uint32_t a_lo = static_cast<uint32_t>(a_base);
+        const uint64_t a_hi = a_base & 0xFFFFFFFF00000000ull;
+        const uint32_t b_lo = static_cast<uint32_t>(b_base);
+        const uint64_t b_hi = b_base & 0xFFFFFFFF00000000ull;
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
           const int ph = (s + ig.coff) & (ig.chain - 1);
@@ -571,18 +582,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sslot = sbase + C::OFF_S + so * C::OPS;
-          const uint32_t bslot = sbase + C::OFF_B + so * C::OPB;
+          const uint32_t a_slot = a_lo + ((static_cast<uint32_t>(so) * C::OPS) >> 4);
+          const uint32_t b_slot = b_lo + ((static_cast<uint32_t>(so) * C::OPB) >> 4);
 #pragma unroll
           for (int ks = 0; ks < KSTEPS; ++ks) {
-            const uint64_t adesc = smem_desc(sslot + ks * S_SLAB, LBO, SBO);
+            const uint64_t adesc = a_hi | (a_slot + ((ks * S_SLAB) >> 4));
 #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
-              for (int h = 0; h < ig.nmma; ++h) {
-                const uint64_t bdesc = smem_desc_sw128(
-                    bslot + static_cast<uint32_t>(pass) * pstride +
-                        static_cast<uint32_t>(h) * hstride + ks * B_KSTEP,
-                    B_LBO, B_SBO);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if (h >= ig.nmma) break;
+                const uint64_t bdesc =
+                    b_hi | (b_slot + ((static_cast<uint32_t>(pass) * pstride +
+                                       static_cast<uint32_t>(h) * hstride + ks * B_KSTEP) >> 4));
                 const uint32_t acc = (!chain_start || ks > 0 || pass > 0) ? 1u : 0u;
                 if (PAIR)
                   mma_bf16_pair(tmem + static_cast<uint32_t>(h) * 256u, adesc, bdesc, idesc, acc);
