@@ -41,6 +41,7 @@ WORKLOADS = {
     "C3": (65536, 16384, 256, (0,), "right"),
     "C4": (None, None, None, (0, 1), "batch"),
     "C5": (None, None, None, (0, 1), "serve"),
+    "NYS": (50000, 50000, None, (0,), "nystrom"),
 }
 DIST_NAME = {0: "gaussian", 1: "rademacher", 2: "uniform"}
 METRIC = "fused gen+sketch TFLOP/s and % roofline vs plain FP32; served p50/p99 latency"
@@ -201,6 +202,8 @@ def run_reference(args):
 
     from paper_2603_20966_gb300.workloads import gaussian_matrix
     m, n, k, dists, side = WORKLOADS[args.workload]
+    if side == "nystrom":  # the pair's first (dominant) product, B = A Omega, r = 500
+        k, side = 500, "right"
     if side == "left":
         ncols, rows = (2, 512) if args.workload == "C2" else (n, k)
         a_part = gaussian_matrix(m, ncols, 1, device="cpu").numpy()
@@ -763,6 +766,96 @@ def run_ours(args):
     return 0
 
 
+def run_nystrom(args):
+    """NYS: the Nystrom pair of the paper's Alg. 2 (B = A Omega, C = Omega^T B,
+    the same Gaussian Omega regenerated by both products) on a 50000 x 50000
+    RBF kernel matrix, r = 500 and r = 5000 (the paper's ranks), BF16 split-A
+    form.  A step is one r; `value` is the r = 500 line, the r = 5000 figures
+    ride along in `ranks`."""
+    import torch
+
+    import paper_2603_20966_gb300 as P
+    from paper_2603_20966_gb300.workloads import rbf_kernel_matrix
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+    n = WORKLOADS["NYS"][0] if args.rows is None else args.rows
+    A = rbf_kernel_matrix(n, seed=21 + rank, device=dev)
+    stream = torch.cuda.Stream(dev)
+    pk, pk_kind = peaks()
+    ranks = {}
+    clocks = ClockSampler(local)
+    clk = None
+    launches = 0
+    for r in (500, 5000):
+        ld = (r + 3) // 4 * 4
+        B = torch.empty((n, ld), dtype=torch.float32, device=dev)
+        C = torch.empty((r, ld), dtype=torch.float32, device=dev)
+        h = P.sk_create(7, 0, r)
+        P.sk_set_precision(h, P.SK_BF16X2)
+        steps = args.steps if r == 500 else max(1, min(args.steps, 10))
+        for _ in range(args.warmup):
+            P.sk_nystrom(h, A, n, n, B, ld, C, ld, stream)
+        if P.sk_stream_status(h, stream) != 0:
+            raise RuntimeError("nystrom status")
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+        if r == 500:
+            clocks.start()
+            launches0 = P.sk_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            P.sk_nystrom(h, A, n, n, B, ld, C, ld, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if r == 500:
+            clk = clocks.stop()
+            launches = P.sk_launch_count() - launches0
+        if P.sk_stream_status(h, stream) != 0:
+            raise RuntimeError("nystrom status after timing")
+        ms = max_over_ranks(e0.elapsed_time(e1), dev) / steps
+        flops = 2.0 * n * n * r + 2.0 * r * n * r
+        # symmetry of C = Omega^T A Omega for a symmetric A (a cheap sanity check)
+        Cs = C[:, :r].double()
+        asym = float((Cs - Cs.t()).norm() / Cs.norm())
+        ranks[r] = {"ms_per_step": ms, "tflops": world * flops / (ms * 1e-3) / 1e12,
+                    "useful_tflop_per_step": flops / 1e12, "c_asymmetry": asym,
+                    "steps": steps}
+        P.sk_destroy(h)
+        del B, C
+    r5 = ranks[500]
+    # both products on the tensor cores: 2 passes x (2 n^2 r + 2 r^2 n) flop
+    roof = {"bound": "tensor", "achieved": 2 * r5["useful_tflop_per_step"] / (r5["ms_per_step"] * 1e-3),
+            "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "peak_kind": f"{pk_kind} bf16 burst",
+            "note": "whole step (right sketch B = A Omega, then left sketch C = Omega^T B), both "
+                    "split-A passes counted", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": r5["tflops"], "unit": "TFLOP/s", "n_gpus": world,
+            "steps": r5["steps"], "warmup": args.warmup, "ms_per_step": r5["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2",
+            "data": "synthetic",
+            "config": {"workload": f"NYS Nystrom pair of a {n}x{n} RBF kernel matrix (50000 "
+                                   "N(0, I_64) points, sigma^2 = |X|_F^2 / n), Gaussian Omega, "
+                                   "r = 500 (line) and 5000 (ranks)",
+                       "n": n, "r": 500, "form": "bf16x2",
+                       "l2": f"inputs larger than L2 (A {n * n * 4 / 2**30:.2f} GiB)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "e2e": None, "gpu_launches": int(launches), "roofline": roof,
+            "cpu_baseline": None, "ranks": ranks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -788,6 +881,8 @@ def main():
         return run_batch(args)
     if WORKLOADS[args.workload][4] == "serve":
         return run_serve(args)
+    if WORKLOADS[args.workload][4] == "nystrom":
+        return run_nystrom(args)
     return run_ours(args)
 
 

@@ -14,6 +14,9 @@ kernel matrices, which are not available):
   C4  256 independent left sketches, m log-uniform in [1024, 65536],
       n uniform in [32, 512], k = 2n, alternating distributions
   C5  Poisson stream of requests drawn like C4 with m up to 2^18
+  NYS the Nystrom pair B = A Omega, C = Omega^T B of a 50000 x 50000 RBF
+      kernel matrix (the shape of the paper's CIFAR-10 experiments), r = 500
+      and 5000
 """
 from __future__ import annotations
 
@@ -55,6 +58,25 @@ def lowrank_plus_noise(m: int, n: int, rank: int = 64, noise: float = 1e-3,
         r1 = min(m, r0 + chunk_rows)
         out[r0:r1].addmm_(U[r0:r1], V.t())
     return out
+
+
+def rbf_kernel_matrix(n: int, d: int = 64, seed: int = 21, device="cpu",
+                      chunk_rows: int = 8192) -> torch.Tensor:
+    """K[n x n] = exp(-|x_i - x_j|^2 / (2 sigma^2)) of n points x_i ~ N(0, I_d),
+    sigma^2 = |X|_F^2 / n (the paper's choice sigma = |X| / sqrt(n)): a dense
+    symmetric positive semi-definite matrix with the structure of the paper's
+    RBF kernel matrices, built in place from the Gram matrix."""
+    X = gaussian_matrix(n, d, seed, device)
+    sq = (X * X).sum(dim=1)
+    inv = -0.5 * n / float(sq.sum())
+    K = torch.empty((n, n), dtype=torch.float32, device=device)
+    for r0 in range(0, n, chunk_rows):
+        r1 = min(n, r0 + chunk_rows)
+        blk = K[r0:r1]
+        torch.mm(X[r0:r1], X.t(), out=blk)
+        blk.mul_(-2.0).add_(sq[r0:r1, None]).add_(sq[None, :]).clamp_(min=0.0)
+        blk.mul_(inv).exp_()
+    return K
 
 
 @dataclass(frozen=True)
