@@ -4,11 +4,13 @@ One step = the left sketches Y = S A of the tall-skinny workload
 (A 2^20 x 512 FP32 ~ N(0,1), k = 2048) with a Rademacher and with a
 Gaussian S, both regenerated inside the kernels from Philox4x32-10.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x2|fp32]
-                  [--impl ours|reference] [--workload C1|C2|C3|C4|C5]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x2|fp32|fp8]
+                  [--impl ours|reference] [--workload C1|C2|C3|C4|C5|NYS]
 
 C1-C3 time single sketches, C4 a batch of 256 sketches in one persistent
-launch, C5 the request server under a Poisson stream (latency percentiles).
+launch, C5 the request server under a Poisson stream (latency percentiles),
+NYS the Nystrom pair (B = A Omega, C = Omega^T B) of a 50000 x 50000 RBF
+kernel matrix.
 
 Prints ONE JSON line (rank 0).  `value` is useful TFLOP/s (2 k m n per
 sketch) over the whole job; `roofline` describes the dominant kernel (the
