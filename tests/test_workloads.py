@@ -27,3 +27,23 @@ def test_serving_stream_shape():
     # log-uniform m: the median is the geometric mean of the ends
     ms = sorted(r.prob.m for r in rs)
     assert ms[len(ms) // 2] == pytest.approx(math.sqrt(1024 * (1 << 18)), rel=0.05)
+
+
+def test_rbf_kernel_matrix_is_the_rbf_kernel():
+    """The Nystrom workload's matrix: entries equal exp(-|x_i - x_j|^2 / (2 sigma^2))
+    of the generated points with sigma^2 = |X|_F^2 / n (checked in FP64 against
+    direct pairwise distances), so it is symmetric, has a unit diagonal and is
+    positive semi-definite."""
+    import numpy as np
+
+    from paper_2603_20966_gb300.workloads import gaussian_matrix, rbf_kernel_matrix
+
+    n, d = 700, 64
+    K = rbf_kernel_matrix(n, d=d, seed=21, chunk_rows=256).double().numpy()
+    X = gaussian_matrix(n, d, 21).double().numpy()
+    sigma2 = (X * X).sum() / n
+    D2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(axis=2)
+    np.testing.assert_allclose(K, np.exp(-D2 / (2 * sigma2)), rtol=0, atol=2e-5)
+    assert np.abs(K - K.T).max() <= 1e-6
+    assert np.abs(np.diag(K) - 1.0).max() <= 1e-5
+    assert np.linalg.eigvalsh(K).min() > -1e-4
