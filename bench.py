@@ -18,9 +18,18 @@ fused sketch kernel) timed with CUDA events recorded by the library's
 measurement hook around each of its launches; `e2e` repeats the step
 through the host-buffer entry points (A copied host->device and Y copied
 back inside the timed region); `cpu_baseline` is the CPU oracle on a
-bounded column sample.  `--impl reference` times the CPU oracle alone.
+bounded sample of whole rows.  `--impl reference` times the CPU oracle alone.
 Under torchrun each rank sketches its own copy of the workload (independent
-problems, no collective on the data path): weak scaling.
+problems, no collective on the data path): weak scaling; with --split the
+ranks share one problem instead (A split by columns for the left sketch, by
+rows for the right, S regenerated on every rank, no data exchange): strong
+scaling.
+
+The C2 line also carries the metric's other legs: `vs_fp32` (the same step in
+the plain FP32 form, and both forms' errors against FP64), `serve` (a
+shortened C5 request stream: p50/p99 latency, served TFLOP/s, both forms) and
+`roofline.generator_floor_ms`.  `cpu_baseline` and --impl reference time the
+oracle on the same sample: whole rows of Y, each against every column.
 """
 from __future__ import annotations
 
@@ -176,6 +185,19 @@ def dist_env():
     return rank, world, local
 
 
+def cpu_sample_rows(workload: str, m: int, k: int, side: str) -> int:
+    """The CPU oracle's sample of one step, the same in the cpu_baseline leg
+    and in --impl reference: whole rows of Y, each against every column of A.
+    Left: that many rows of Y = S A, each one S row generated once and used by
+    all n columns, as in the full workload.  Right: that many rows of A, all k
+    columns of Y each, with S generated once for the call (the full workload
+    spreads it over m rows, so the sample is large enough for the product to
+    dominate)."""
+    if side == "left":
+        return min(k, 64)
+    return min(m, 1024)
+
+
 def oracle_sample(m, n, k, dists, a_part, seed, rows, nthreads=None, side="left"):
     """Time the CPU oracle on a sample of Y for each distribution.  Left:
     `rows` rows of Y x the a_part.shape[1] columns of A given.  Right: all k
@@ -195,6 +217,86 @@ def oracle_sample(m, n, k, dists, a_part, seed, rows, nthreads=None, side="left"
     return dt, 2.0 * a_part.shape[0] * n * k * len(dists), nthreads
 
 
+def generator_floor(dist: int, entries: float, sm_mhz: float, sms: int):
+    """Issue-rate floor of generating `entries` entries of S: the generator's
+    thread instructions per entry (from the committed ncu summary of the left
+    kernel, or None when that kernel's source changed since) over the issue
+    rate of every SM (4 schedulers x 32 lanes per cycle).  Returns (ms,
+    instructions per entry) or None."""
+    if dist != 0:
+        return None  # sign bits: one Philox word per 32 entries, not separable
+    prof = os.path.join(ROOT, "profiles", "k_sketch_bf16x2_left_pair_m2e18.md")
+    sha = left_kernel_source_sha()
+    try:
+        text = open(prof).read()
+    except OSError:
+        return None
+    key = "gaussian_thread_instructions_per_entry"
+    rec = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and
+               line.split(": ", 1)[0] in ("left_kernel_source_sha256_16", key))
+    if sha is None or rec.get("left_kernel_source_sha256_16") != sha or key not in rec:
+        return None
+    ipe = float(rec[key])
+    return entries * ipe / (sms * 128 * sm_mhz * 1e6) * 1e3, ipe
+
+
+def fp32_comparison(P, A, m, n, k, dists, Ys, stream, steps, ncols=32):
+    """The metric's comparison: the same left-sketch step in the plain FP32
+    form (FP32 FMA on the CUDA cores), timed with CUDA events, and the error
+    of both forms against FP64 products of their own S (g for FP32, bf16(g)
+    for BF16 split-A, materialized by the library in row blocks of A) over
+    `ncols` evenly spaced columns of Y."""
+    import numpy as np
+    import torch
+    dev = A.device
+    hs = {d: P.sk_create(7, d, k) for d in dists}  # FP32 is the default form
+    Y32 = {d: torch.empty((k, n), dtype=torch.float32, device=dev) for d in dists}
+
+    def step():
+        for d in dists:
+            P.sk_apply_left(hs[d], A, m, n, n, Y32[d], n, stream)
+
+    step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    for d in dists:
+        if P.sk_stream_status(hs[d], stream) != 0:
+            raise RuntimeError("FP32 comparison: device status")
+    cols = torch.from_numpy(np.linspace(0, n - 1, ncols).astype(np.int64)).to(dev)
+    A64 = A[:, cols].double()
+    block = 1 << 18
+    err = {"bf16x2": {}, "fp32": {}}
+    for d in dists:
+        s = P.sk_get_info(hs[d])["scale"]
+        ref32 = torch.zeros((k, ncols), dtype=torch.float64, device=dev)
+        ref16 = torch.zeros((k, ncols), dtype=torch.float64, device=dev)
+        for c0 in range(0, m, block):
+            w = min(block, m - c0)
+            S = torch.empty((k, w), dtype=torch.float32, device=dev)
+            P.sk_materialize(hs[d], 0, c0, k, w, P.SK_FP32, 0, S, w, stream)
+            ref32 += S.double() @ A64[c0:c0 + w]
+            Sb = torch.empty((k, w), dtype=torch.bfloat16, device=dev)
+            P.sk_materialize(hs[d], 0, c0, k, w, P.SK_BF16X2, 0, Sb, w, stream)
+            ref16 += Sb.double() @ A64[c0:c0 + w]
+            del S, Sb
+        ref32 *= s
+        ref16 *= s
+        name = DIST_NAME[d]
+        err["fp32"][name] = float((Y32[d][:, cols].double() - ref32).norm() / ref32.norm())
+        err["bf16x2"][name] = float((Ys[d][:, cols].double() - ref16).norm() / ref16.norm())
+        del ref32, ref16
+    for d in dists:
+        P.sk_destroy(hs[d])
+    del Y32, A64
+    return ms, err
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed on a bounded sample per step."""
     rank, world, _ = dist_env()
@@ -206,12 +308,15 @@ def run_reference(args):
     m, n, k, dists, side = WORKLOADS[args.workload]
     if side == "nystrom":  # the pair's first (dominant) product, B = A Omega, r = 500
         k, side = 500, "right"
+    if side not in ("left", "right"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"workload {args.workload} has no CPU oracle leg (batch/serving)"}))
+        return 0
+    rows = cpu_sample_rows(args.workload, m, k, side)
     if side == "left":
-        ncols, rows = (2, 512) if args.workload == "C2" else (n, k)
-        a_part = gaussian_matrix(m, ncols, 1, device="cpu").numpy()
-        what = f"{rows} of {k} rows x {ncols} of {n} columns of Y"
+        a_part = gaussian_matrix(m, n, 1, device="cpu").numpy()
+        what = f"{rows} of {k} rows x all {n} columns of Y"
     else:
-        rows = 16
         a_part = gaussian_matrix(rows, n, 1, device="cpu").numpy()
         what = f"{rows} of {m} rows x all {k} columns of Y"
     for _ in range(args.warmup):
@@ -230,7 +335,8 @@ def run_reference(args):
         "config": {"workload": f"{args.workload} {side} sketch A {m}x{n} k={k} "
                    f"dists={[DIST_NAME[d] for d in dists]}", "m": m, "n": n, "k": k},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{what} per distribution per step (FP64 accumulation)"},
+                         "sample": f"{what} per distribution per step (FP64 accumulation); "
+                                   "the rate of whole rows, not extrapolated"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -388,38 +494,16 @@ def _serve_stream(P, srv, reqs, hs, src_ptr, src_ld, fetch=None):
     return wall, late
 
 
-def run_serve(args):
-    """C5: a Poisson stream of left-sketch requests (2000/s, m log-uniform in
-    [1024, 2^18], n uniform in [32, 512], k = 2n) through the request server
-    with a 120 GB budget; BF16 split-A and plain FP32 forms; p50/p99 latency
-    (arrival to Y ready) and served useful TFLOP/s."""
+def serve_forms(P, reqs, forms, src, src_host, src_ld, warmup, world, clocks=None,
+                e2e_leg=False):
+    """Run the request stream `reqs` through a server once per form (name,
+    sk_precision) with a 120 GB budget.  Returns ({form: latency and
+    throughput figures}, clock record of the first form, end-to-end record
+    or None, kernel launches)."""
     import torch
-
-    import paper_2603_20966_gb300 as P
-    from paper_2603_20966_gb300.workloads import gaussian_matrix, serving_requests
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl", device_id=dev)
-    count = args.serve_requests
-    reqs = serving_requests(count, seed=3000 + 1000 * rank)
-    src_rows, src_ld = 1 << 18, 512
-    # the load generator's source rows: every request reads a window of them
-    src = gaussian_matrix(src_rows, src_ld, 77 + rank, device=dev)
-    src_host = torch.empty((src_rows, src_ld), dtype=torch.float32, pin_memory=True)
-    src_host.copy_(src)
-    torch.cuda.synchronize(dev)
     budget = 120 * 10**9
-    forms = [("bf16x2", P.SK_BF16X2), ("fp32", P.SK_FP32)]
-    out = {}
-    launches = 0
-    clocks = ClockSampler(local)
-    clk = None
-    e2e = None
-    for name, form in forms:
+    out, clk, e2e, launches = {}, None, None, 0
+    for fi, (name, form) in enumerate(forms):
         hs = []
         for r in reqs:
             h = P.sk_create(r.prob.seed, r.prob.dist, r.prob.k)
@@ -428,19 +512,20 @@ def run_serve(args):
             hs.append(h)
         srv = P.sk_server_create(budget, 4096)
         try:
-            # warm-up: one request of each distinct small shape class
-            warm = reqs[:max(3, args.warmup) * 10]
+            # warm-up: the first requests once, all at time zero
+            warm = reqs[:max(3, warmup) * 10]
             _serve_stream(P, srv, [type(r)(0.0, r.prob, r.row0) for r in warm], hs,
                           src.data_ptr(), src_ld)
             P.sk_server_reset_stats(srv)
             if world > 1:
+                import torch.distributed as tdist
                 tdist.barrier()
-            if name == "bf16x2":
+            if fi == 0 and clocks is not None:
                 clocks.start()
             l0 = P.sk_launch_count()
             wall, late = _serve_stream(P, srv, reqs, hs, src.data_ptr(), src_ld)
             launches += P.sk_launch_count() - l0
-            if name == "bf16x2":
+            if fi == 0 and clocks is not None:
                 clk = clocks.stop()
             st = P.sk_server_stats_get(srv)
             out[name] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
@@ -448,11 +533,11 @@ def run_serve(args):
                          "mean_wait_ms": st["mean_wait_ms"],
                          "served_tflops": st["flops"] / wall / 1e12,
                          "wall_s": wall, "steps": st["steps"],
-                         "mean_requests_per_step": count / max(1, st["steps"]),
+                         "mean_requests_per_step": len(reqs) / max(1, st["steps"]),
                          "max_step_requests": st["max_step_requests"],
                          "peak_pool_gb": st["peak_bytes"] / 1e9,
                          "max_submit_lateness_ms": late * 1e3}
-            if name == "bf16x2" and not args.no_e2e:
+            if fi == 0 and e2e_leg:
                 # end to end: sources in pinned host memory (copied in at
                 # admission), every Y fetched back to pinned host memory
                 P.sk_server_reset_stats(srv)
@@ -464,12 +549,53 @@ def run_serve(args):
                        "h2d_bytes_per_step": sum(4 * r.prob.m * r.prob.n for r in reqs),
                        "d2h_bytes_per_step": sum(4 * r.prob.k * r.prob.n for r in reqs),
                        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "wall_s": wall_e,
-                       "step": f"the whole {count}-request stream from pinned host sources, "
-                               "results fetched to pinned host memory"}
+                       "step": f"the whole {len(reqs)}-request stream from pinned host "
+                               "sources, results fetched to pinned host memory"}
         finally:
             P.sk_server_destroy(srv)
             for h in hs:
                 P.sk_destroy(h)
+    return out, clk, e2e, launches
+
+
+def serve_source(dev, rank, pinned=True):
+    """The load generator's source rows (every request reads a window of
+    them): 2^18 x 512 N(0,1) on the device, and a pinned host copy."""
+    import torch
+    from paper_2603_20966_gb300.workloads import gaussian_matrix
+    src_rows, src_ld = 1 << 18, 512
+    src = gaussian_matrix(src_rows, src_ld, 77 + rank, device=dev)
+    src_host = None
+    if pinned:
+        src_host = torch.empty((src_rows, src_ld), dtype=torch.float32, pin_memory=True)
+        src_host.copy_(src)
+    torch.cuda.synchronize(dev)
+    return src, src_host, src_ld
+
+
+def run_serve(args):
+    """C5: a Poisson stream of left-sketch requests (2000/s, m log-uniform in
+    [1024, 2^18], n uniform in [32, 512], k = 2n) through the request server
+    with a 120 GB budget; BF16 split-A and plain FP32 forms; p50/p99 latency
+    (arrival to Y ready) and served useful TFLOP/s."""
+    import torch
+
+    import paper_2603_20966_gb300 as P
+    from paper_2603_20966_gb300.workloads import serving_requests
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+    count = args.serve_requests
+    reqs = serving_requests(count, seed=3000 + 1000 * rank)
+    src, src_host, src_ld = serve_source(dev, rank)
+    clocks = ClockSampler(local)
+    out, clk, e2e, launches = serve_forms(
+        P, reqs, [("bf16x2", P.SK_BF16X2), ("fp32", P.SK_FP32)], src, src_host, src_ld,
+        args.warmup, world, clocks=clocks, e2e_leg=not args.no_e2e)
     flops = sum(2.0 * r.prob.k * r.prob.m * r.prob.n for r in reqs)
     offered = flops / reqs[-1].arrival_s / 1e12
     if rank == 0:
@@ -532,10 +658,30 @@ def run_ours(args):
     for d in dists:
         hs[d] = P.sk_create(7, d, k)
         P.sk_set_precision(hs[d], form)
+    # what this rank computes: the whole problem (replicas), or with --split
+    # its block of one problem shared by all ranks (the paper's Case 1: A split
+    # by columns for the left sketch, by rows for the right; every rank
+    # regenerates the same S; no data exchange)
+    A_run, m_run, n_run, lda_run = A, m, n, n
+    Y_run = dict(Ys)
+    part = None
+    if args.split:
+        from paper_2603_20966_gb300.partition import left_column_ranges, right_row_ranges
+        if side == "left":
+            c0, c1 = left_column_ranges(n, world)[rank]
+            A_run, n_run = A[:, c0:c1], c1 - c0
+            Y_run = {d: Ys[d][:, c0:c1] for d in dists}
+            part = {"columns": [c0, c1]}
+        else:
+            r0, r1 = right_row_ranges(m, world)[rank]
+            A_run, m_run = A[r0:r1], r1 - r0
+            Y_run = {d: Ys[d][r0:r1] for d in dists}
+            part = {"rows": [r0, r1]}
+    ldy_run = yshape[1]
 
     def step():
         for d in dists:
-            apply(hs[d], A, m, n, n, Ys[d], yshape[1], stream)
+            apply(hs[d], A_run, m_run, n_run, lda_run, Y_run[d], ldy_run, stream)
 
     for _ in range(args.warmup):
         step()
@@ -567,7 +713,7 @@ def run_ours(args):
     for _ in range(args.steps):
         for d in dists:
             P.sk_profile_events(hs[d], ev[i][0], ev[i][1])
-            apply(hs[d], A, m, n, n, Ys[d], yshape[1], stream)
+            apply(hs[d], A_run, m_run, n_run, lda_run, Y_run[d], ldy_run, stream)
             i += 1
     t_stop.record(stream)
     torch.cuda.synchronize(dev)
@@ -582,9 +728,11 @@ def run_ours(args):
             raise RuntimeError(f"device status after timing: {P.status_string(st)}")
     ms = max_over_ranks(t_start.elapsed_time(t_stop), dev)
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
-    flops_per_sketch = 2.0 * k * m * n
+    flops_per_sketch = 2.0 * k * m_run * n_run  # this rank's sketch (or block of one)
     flops_step = flops_per_sketch * len(dists)
-    value = world * flops_step * args.steps / (ms * 1e-3) / 1e12
+    # whole job: N replicas of the problem, or one problem split over N ranks
+    job_flops_step = (2.0 * k * m * n * len(dists)) if args.split else world * flops_step
+    value = job_flops_step * args.steps / (ms * 1e-3) / 1e12
 
     pk, pk_kind = peaks()
     avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
@@ -605,7 +753,7 @@ def run_ours(args):
                         "codes written once)"}
     elif side == "right":
         # HBM-bound: A read once, Y written once
-        algo_bytes = 4.0 * m * n + 4.0 * m * k
+        algo_bytes = 4.0 * m_run * n_run + 4.0 * m_run * k
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": algo_bytes / avg_kernel_s / 1e9, "peak": peak,
                 "unit": "GB/s", "peak_kind": f"{pk_kind} copy bandwidth",
@@ -629,7 +777,7 @@ def run_ours(args):
                                  for j, d in enumerate(dists)}
 
     fp8 = None
-    if form == P.SK_FP8E4M3:
+    if form == P.SK_FP8E4M3 and not args.split:
         # a resident quantized A (quantized once, outside the timed region)
         ldq = (n + 15) // 16 * 16
         Aq = torch.empty((m, ldq), dtype=torch.uint8, device=dev)
@@ -657,7 +805,7 @@ def run_ours(args):
     # generate versus communicate (Sec. 6.2): the same kernel reading a
     # materialized BF16 S from HBM instead of generating it
     ablation = None
-    if form == P.SK_BF16X2 and side == "left" and not args.no_ablation:
+    if form == P.SK_BF16X2 and side == "left" and not args.no_ablation and not args.split:
         lds = (m + 15) // 16 * 16
         ablation = {"S_bytes": 2 * k * lds, "fused_kernel_ms": {}, "stored_kernel_ms": {},
                     "materialize_ms": {}, "identical_to_fused": {},
@@ -696,16 +844,70 @@ def run_ours(args):
             ablation["identical_to_fused"][name] = bool(torch.equal(Yst, Ys[d]))
             del S, Yst
 
+    # the metric's other legs: the same step in plain FP32, with the error of
+    # both forms against FP64 measured in this run; the served latencies of a
+    # shortened C5 stream; the generator's issue-rate floor
+    vs_fp32 = None
+    if (form == P.SK_BF16X2 and side == "left" and args.rows is None and not args.no_fp32 and
+            not args.split):
+        fms, ferr = fp32_comparison(P, A, m, n, k, dists, Ys, stream, args.fp32_steps)
+        fp32_tflops = world * flops_step / (fms * 1e-3) / 1e12
+        vs_fp32 = {"fp32_tflops": fp32_tflops, "fp32_ms_per_step": fms,
+                   "bf16x2_over_fp32": value / fp32_tflops,
+                   "fp32_steps": args.fp32_steps, "err_vs_fp64": ferr,
+                   "err_note": "relative Frobenius error of Y over 32 evenly spaced columns "
+                               "against FP64 products with each form's own S (g for FP32, "
+                               "bf16(g) for BF16 split-A) materialized by the library; "
+                               "tolerance 1e-5",
+                   "fp32_form": "FP32 FMA on the CUDA cores, S generated in shared memory"}
+    if roof.get("bound") == "tensor":
+        clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        floors = {}
+        for d in dists:
+            f = generator_floor(d, float(k) * float(m), clk_mhz, sms)
+            if f is not None:
+                floors[DIST_NAME[d]] = {"ms": f[0], "thread_instructions_per_entry": f[1]}
+        roof["generator_floor_ms"] = ({nm: v["ms"] for nm, v in floors.items()}
+                                      if floors else None)
+        if floors:
+            roof["generator_floor_note"] = (
+                "entries x the generator's thread instructions per entry (committed ncu "
+                "summary of this kernel source) / (SMs x 128 issue lanes x median SM clock): "
+                f"{floors}")
+    serve = None
+    if (args.workload == "C2" and args.rows is None and args.serve_leg_requests > 0 and
+            not args.split):
+        from paper_2603_20966_gb300.workloads import serving_requests
+        reqs = serving_requests(args.serve_leg_requests, seed=3000 + 1000 * rank)
+        src, _, src_ld = serve_source(dev, rank, pinned=False)
+        sout, _, _, _ = serve_forms(P, reqs, [("bf16x2", P.SK_BF16X2), ("fp32", P.SK_FP32)],
+                                    src, None, src_ld, 3, world)
+        del src
+        fl = sum(2.0 * r.prob.k * r.prob.m * r.prob.n for r in reqs)
+        serve = {"requests": len(reqs), "rate_per_s": 2000.0,
+                 "offered_tflops": fl / reqs[-1].arrival_s / 1e12,
+                 "latency_ms": {f: {"p50": sout[f]["p50_ms"], "p99": sout[f]["p99_ms"]}
+                                for f in sout},
+                 "served_tflops": {f: sout[f]["served_tflops"] for f in sout},
+                 "forms": sout,
+                 "note": f"shortened C5 stream: the first {len(reqs)} of its 20000 requests "
+                         "(Poisson arrivals at 2000/s, m log-uniform [1024, 2^18], n uniform "
+                         "[32, 512], k = 2n, 120 GB budget); latency = arrival to Y ready; "
+                         "the full stream is bench.py --workload C5"}
+
     # end to end through the host-buffer entry points
     e2e = None
     if not args.no_e2e:
-        A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
-        A_host.copy_(A)
-        Y_host = {d: torch.empty(yshape, dtype=torch.float32, pin_memory=True) for d in dists}
+        # this rank's block of A in pinned host memory, its block of Y back
+        A_host = torch.empty((m_run, n_run), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A_run)
+        yb = (k, n_run) if side == "left" else (m_run, k)
+        Y_host = {d: torch.empty(yb, dtype=torch.float32, pin_memory=True) for d in dists}
 
         def e2e_step():
             for d in dists:
-                apply_host(hs[d], A_host, m, n, n, Y_host[d], yshape[1], stream)
+                apply_host(hs[d], A_host, m_run, n_run, n_run, Y_host[d], yb[1], stream)
 
         for _ in range(max(1, min(args.warmup, 2))):
             e2e_step()
@@ -716,28 +918,28 @@ def run_ours(args):
         for _ in range(e_steps):
             e2e_step()
         dt = max_over_ranks(time.perf_counter() - t0, dev)
-        e2e = {"value": world * flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": len(dists) * m * n * 4,
-               "d2h_bytes_per_step": len(dists) * yshape[0] * yshape[1] * 4, "steps": e_steps,
+        e2e = {"value": job_flops_step * e_steps / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": len(dists) * m_run * n_run * 4,
+               "d2h_bytes_per_step": len(dists) * yb[0] * yb[1] * 4, "steps": e_steps,
                "ms_per_step": dt / e_steps * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = cpu_sample_rows(args.workload, m, k, side)
         if side == "left":
-            ncols, rows = (16, 2048) if args.workload == "C2" else (n, k)
-            cols = np.linspace(0, n - 1, ncols).astype(np.int64)
-            a_part = A[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
-            what = f"{rows} of {k} rows x {ncols} of {n} columns of Y"
+            a_part = A.cpu().numpy()
+            what = f"{rows} of {k} rows x all {n} columns of Y"
         else:
-            rows = 256
             idx = np.linspace(0, m - 1, rows).astype(np.int64)
             a_part = A[torch.from_numpy(idx).to(dev)].cpu().numpy()
             what = f"{rows} of {m} rows x all {k} columns of Y"
         dt, fl, threads = oracle_sample(m, n, k, dists, a_part, 7, rows, side=side)
         cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                "sample": f"{what} for each of {[DIST_NAME[d] for d in dists]} "
-                         f"(FP64 accumulation), {dt:.1f} s; rate extrapolates to the full "
-                         f"workload"}
+                         f"(FP64 accumulation), {dt:.1f} s; whole rows, each S row generated "
+                         f"once for all columns as in the full workload (the --impl "
+                         f"reference sample); the rate of the sample, not extrapolated"}
+        del a_part
 
     for d in dists:
         P.sk_destroy(hs[d])
@@ -745,7 +947,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.split else "weak",
+            "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16x2": "bf16x2", "fp8": "e4m3"}[args.form],
             "data": "synthetic",
             "config": {"workload": f"{args.workload} {side} sketch A {m}x{n} FP32 "
@@ -754,10 +957,19 @@ def run_ours(args):
                                    f"seed 7",
                        "m": m, "n": n, "k": k, "form": args.form,
                        "l2": f"inputs larger than L2 (A {m * n * 4 / 2**30:.2f} GiB)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"split x{world}: one problem, A by "
+                                       f"{'columns' if side == 'left' else 'rows'}, S "
+                                       f"regenerated on every rank, no data exchange"
+                                       if args.split else f"replicas x{world}")},
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
             "cpu_baseline": cpu,
         }
+        if part is not None:
+            line["config"]["rank0_block"] = part
+        if vs_fp32 is not None:
+            line["vs_fp32"] = vs_fp32
+        if serve is not None:
+            line["serve"] = serve
         if fp8 is not None:
             line["fp8"] = fp8
         if ablation is not None:
@@ -871,6 +1083,15 @@ def main():
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the stored-S (generate versus communicate) comparison")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-leg-requests", type=int, default=4000,
+                    help="requests of the shortened C5 stream in the C2 line (0: none)")
+    ap.add_argument("--no-fp32", action="store_true",
+                    help="skip the FP32 comparison leg of the C2 line")
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--split", action="store_true",
+                    help="C1-C3 under torchrun: one problem split over the ranks (A by columns "
+                         "for the left sketch, by rows for the right; strong scaling) instead "
+                         "of one problem per rank")
     ap.add_argument("--rows", type=int, default=None,
                     help="rows of A (C1-C3): a smaller case of the workload, for ncu captures")
     ap.add_argument("--dists", default=None, help="comma-separated distributions (0 G, 1 R, 2 U)")

@@ -105,7 +105,10 @@ sk_status sk_get_info(sk_handle h, uint64_t* seed, int* dist, int64_t* k, int* p
  * Y: k x n, leading dim ldy >= n; both device pointers, FP32).  S(r, c)
  * for r < k, c < m.  Requires m < 2^32.  The tensor-core forms additionally
  * require A and Y 16-byte aligned and lda, ldy multiples of 4 (SK_EINVAL
- * otherwise).  Y is fully overwritten.  A and Y must not overlap. */
+ * otherwise).  Y is fully overwritten.  A and Y must not overlap.
+ * In the SK_FP32 form k is at most 8,388,480 (65535 launch tiles of 128
+ * rows of S); CUDA rejects the launch of a larger k and the call returns
+ * SK_ECUDA (nothing runs). */
 sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda, float* Y,
                         int64_t ldy, void* stream);
 
@@ -178,13 +181,17 @@ sk_status sk_apply_right_e4m3(sk_handle h, const uint8_t* Aq, const int32_t* row
  * that loads the library holds until the process exits.  Problems whose
  * partials would exceed it -- splits * k * n * 4 bytes > 16 MiB, with
  * sk_workspace_size(h, 0, m, n) reporting that byte count -- are rejected
- * with SK_EUNSUPPORTED before anything is enqueued.  The first call on each
- * device looks up that device's address of the array (set-up that
- * allocates nothing); make that first call before any stream capture.
+ * with SK_EUNSUPPORTED before anything is enqueued.  Every call looks up the
+ * current device's address of the array (cudaGetSymbolAddress, which
+ * allocates nothing), so the address stays right after a cudaDeviceReset;
+ * on a device's first call the CUDA runtime may load the library's device
+ * code, so make that first call before any stream capture.
  * All calls on a device share the array and each call writes every partial
  * it later reads, so nothing needs clearing between calls, but calls whose
  * work overlaps on the GPU (different streams, no ordering) race on it and
- * give undefined results: order them on one stream or with events. */
+ * give undefined results: order them on one stream or with events.
+ * Errors: SK_EINVAL, SK_EUNSUPPORTED, SK_ECUDA (sk_last_cuda_error then
+ * describes the failing CUDA call, as for every other entry point). */
 sk_status sk_apply_left_noalloc(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda,
                                 float* Y, int64_t ldy, void* stream);
 
@@ -410,6 +417,20 @@ sk_status sk_server_destroy(sk_server_handle s);
  * accumulation chain) it was waiting for, [3] the linear index of its CTA.
  * Words 1-3 are meaningful only when word 0 is SK_ETIMEOUT. */
 sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]);
+
+/* Failure injection for tests of the bounded waits above (not in the paper;
+ * it lets a test make a device wait run out without faulting anything).
+ * limit_ns: the limit of every bounded wait of the handle's later tensor-
+ * core launches, at least 1 ms; 0 restores the default of 2 s.
+ * stall_stage >= 0: in later BF16 left sketches on this handle the TMA
+ * producer issues no copy for that pipeline stage (stages counted from 0
+ * over each CTA's, or CTA pair's, run of a launch), so every wait that
+ * depends on it gives up after
+ * limit_ns: the kernel records SK_ETIMEOUT and the waiting site (see
+ * sk_debug_status), waits (again bounded) for the copies and MMAs already
+ * in flight, frees its tensor memory and exits; Y is then undefined.
+ * stall_stage < 0 turns the injection off.  Errors: SK_EINVAL. */
+sk_status sk_debug_set_wait(sk_handle h, uint64_t limit_ns, int64_t stall_stage);
 
 /* Release the handle and the device memory it owns.  Waits for nothing:
  * the caller must ensure no enqueued work still uses it. */

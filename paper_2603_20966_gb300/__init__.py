@@ -11,7 +11,7 @@ from __future__ import annotations
 from ._native import (SK_BF16X2, sk_batch_add, sk_batch_create, sk_batch_destroy,
                       sk_batch_run, sk_batch_size, sk_batch_status, sk_batch_tune, SK_FP8E4M3, SK_FP32, SK_GAUSSIAN, SK_RADEMACHER, SK_UNIFORM,
                       SketchError, sk_apply_left, sk_apply_left_host, sk_apply_right,
-                      sk_apply_right_host, sk_create, sk_debug_status, sk_destroy, sk_get_info, sk_launch_count, sk_materialize,
+                      sk_apply_right_host, sk_create, sk_debug_set_wait, sk_debug_status, sk_destroy, sk_get_info, sk_launch_count, sk_materialize,
                       sk_profile_events,
                       sk_set_precision, sk_set_workspace, sk_stream_status, sk_version,
                       sk_workspace_size, status_string)
@@ -26,7 +26,8 @@ __all__ = [
     "Sketch", "SketchError", "SK_GAUSSIAN", "SK_RADEMACHER", "SK_UNIFORM", "SK_FP32", "SK_BF16X2",
     "SK_FP8E4M3", "sk_create", "sk_set_precision", "sk_get_info", "sk_apply_left",
     "sk_apply_right", "sk_apply_left_host", "sk_apply_right_host", "sk_materialize",
-    "sk_workspace_size", "sk_set_workspace", "sk_stream_status", "sk_debug_status", "sk_destroy", "sk_version", "sk_profile_events", "sk_launch_count",
+    "sk_workspace_size", "sk_set_workspace", "sk_stream_status", "sk_debug_status",
+    "sk_debug_set_wait", "sk_destroy", "sk_version", "sk_profile_events", "sk_launch_count",
     "status_string", "sk_batch_create", "sk_batch_add", "sk_batch_run", "sk_batch_tune",
     "sk_batch_status", "sk_batch_size", "sk_batch_destroy", "Server", "sk_server_create",
     "sk_server_submit", "sk_server_poll", "sk_server_wait", "sk_server_fetch",

@@ -38,6 +38,7 @@ PROTOTYPES = {
     "sk_set_workspace": (_int, [_vp, _vp, _sz]),
     "sk_stream_status": (_int, [_vp, _vp]),
     "sk_debug_status": (_int, [_vp, _vp, _P(ctypes.c_int32)]),
+    "sk_debug_set_wait": (_int, [_vp, _u64, _i64]),
     "sk_batch_create": (_int, [_P(_vp)]),
     "sk_batch_add": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64]),
     "sk_batch_run": (_int, [_vp, _vp]),
@@ -240,6 +241,12 @@ def sk_debug_status(h, stream=None) -> list[int]:
     out = (ctypes.c_int32 * 4)()
     _check("sk_debug_status", _lib.sk_debug_status(h, _stream(stream), out))
     return list(out)
+
+
+def sk_debug_set_wait(h, limit_ns: int = 0, stall_stage: int = -1) -> None:
+    """Failure-injection hook of the tests: bounded-wait limit (0 = default)
+    and a pipeline stage whose copy is never issued (-1 = none); see sketch.h."""
+    _check("sk_debug_set_wait", _lib.sk_debug_set_wait(h, int(limit_ns), int(stall_stage)))
 
 
 def sk_batch_create() -> int:

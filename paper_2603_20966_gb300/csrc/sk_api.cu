@@ -169,6 +169,8 @@ sk_status sk_create(uint64_t seed, int dist, int64_t k, sk_handle* out) {
   h->k = k;
   h->prec = SK_FP32;
   h->scale = 1.0f / sqrtf((float)k);  // both operations IEEE round-to-nearest
+  h->wait_limit_ns = sk::kDefaultWaitLimitNs;
+  h->stall_stage = -1;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
@@ -331,6 +333,14 @@ sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) e = cudaMemcpy(out, h->d_status, sizeof(int) * 4, cudaMemcpyDeviceToHost);
   return from_cuda(e);
+}
+
+sk_status sk_debug_set_wait(sk_handle h, uint64_t limit_ns, int64_t stall_stage) {
+  if (!h) return SK_EINVAL;
+  if (limit_ns != 0 && limit_ns < 1000000ull) return SK_EINVAL;  // at least 1 ms
+  h->wait_limit_ns = limit_ns ? limit_ns : sk::kDefaultWaitLimitNs;
+  h->stall_stage = stall_stage < 0 ? -1 : stall_stage;
+  return SK_OK;
 }
 
 sk_status sk_destroy(sk_handle h) {

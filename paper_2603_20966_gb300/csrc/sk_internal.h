@@ -26,7 +26,15 @@ struct sk_sketch {
   void* d_sched;           // device copy of the tensor-core work list (problem + items)
   size_t d_sched_bytes;
   uint64_t sched_key[9];   // what the uploaded work list was built for
+  uint64_t wait_limit_ns;  // limit of every bounded device wait (sk_debug_set_wait)
+  int64_t stall_stage;     // injected stall of the tests (sk_debug_set_wait), or -1
 };
+
+namespace sk {
+// Limit of a bounded device wait unless a test shortens it: far beyond any
+// healthy stage, short enough that a stuck kernel returns within seconds.
+constexpr uint64_t kDefaultWaitLimitNs = 2000000000ull;
+}  // namespace sk
 
 namespace sk {
 

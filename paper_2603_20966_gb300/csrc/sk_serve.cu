@@ -3,8 +3,11 @@
 // overlapping compute streams, per-request latency.
 //
 // One scheduler thread owns every CUDA call of the server except the event
-// recorded at submission and the copy of a result out (sk_server_fetch).  Request state lives in one map guarded by
-// one mutex; the scheduler drops the mutex only while it waits.
+// recorded at submission and the copy of a result out (sk_server_fetch).
+// Request state lives in one map guarded by one mutex; the scheduler drops
+// the mutex while it issues CUDA work and while it sleeps.  While a step is
+// in flight the scheduler sleeps: a host function enqueued behind each step
+// wakes it when the step has finished.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -149,6 +152,11 @@ struct Lane {
   int* h_status = nullptr;  // pinned copy of the lane's status word
   bool busy = false;
   std::vector<int64_t> tickets;
+  // completion signal of the step in flight: a host function enqueued after
+  // the step records when it ran and wakes the scheduler (under mu)
+  uint64_t seq = 0;  // steps launched on this lane
+  bool signalled = false;
+  Clock::time_point t_signal;
 };
 
 }  // namespace
@@ -194,6 +202,34 @@ struct sk_server {
   void free_work(Request& r);
   void free_y(Request& r);
 };
+
+namespace {
+
+// Argument of the completion host function of one step.
+struct StepSignal {
+  sk_server* s;
+  Lane* ln;
+  uint64_t seq;
+};
+
+// Runs on a CUDA runtime thread once everything enqueued before it on the
+// lane's stream has finished (no CUDA calls here).  Records the time for the
+// step it belongs to and wakes the scheduler, which otherwise sleeps while a
+// step is in flight.
+void CUDART_CB step_done_host_fn(void* p) {
+  StepSignal* sg = static_cast<StepSignal*>(p);
+  {
+    std::lock_guard<std::mutex> g(sg->s->mu);
+    if (sg->ln->seq == sg->seq) {
+      sg->ln->signalled = true;
+      sg->ln->t_signal = Clock::now();
+    }
+  }
+  sg->s->work_cv.notify_one();
+  delete sg;
+}
+
+}  // namespace
 
 // Copy A[m x n] (row stride lds) into the pool (row stride ldd): one warp
 // per row, consecutive lanes on consecutive columns.  The source may be
@@ -272,7 +308,9 @@ bool sk_server::retire_lanes(std::unique_lock<std::mutex>&) {
     if (!ln.busy) continue;
     const cudaError_t q = cudaEventQuery(ln.done);
     if (q == cudaErrorNotReady) continue;
-    const Clock::time_point now = Clock::now();
+    // the step's host function ran when it finished (it may still be on its
+    // way if the event was seen first)
+    const Clock::time_point now = ln.signalled ? ln.t_signal : Clock::now();
     sk_status err = SK_OK;
     if (q != cudaSuccess) {
       err = sk::status_from_cuda(q);
@@ -354,6 +392,8 @@ std::vector<StepItem> sk_server::take_step_locked(Lane* ln) {
   }
   admitted.erase(admitted.begin(), admitted.begin() + take);
   ln->busy = true;
+  ++ln->seq;
+  ln->signalled = false;
   ++steps;
   max_step = std::max<int64_t>(max_step, static_cast<int64_t>(take));
   return items;
@@ -382,6 +422,8 @@ cudaError_t sk_server::launch_items(Lane* ln, const std::vector<StepItem>& items
     h.scale = it.mb.scale;
     h.device = device;
     h.d_status = ln->arena.d_status;
+    h.wait_limit_ns = sk::kDefaultWaitLimitNs;
+    h.stall_stage = -1;
     sk::GemmShape s;
     s.left = true;
     s.P = it.mb.k;
@@ -394,6 +436,18 @@ cudaError_t sk_server::launch_items(Lane* ln, const std::vector<StepItem>& items
     e = cudaMemcpyAsync(ln->h_status, ln->arena.d_status, sizeof(int), cudaMemcpyDeviceToHost,
                         ln->st);
   if (e == cudaSuccess) e = cudaEventRecord(ln->done, ln->st);
+  if (e == cudaSuccess) {
+    // wake the scheduler when the step has finished; if this cannot be
+    // enqueued the scheduler still polls the event, at a slower cadence
+    StepSignal* sg = new (std::nothrow) StepSignal;
+    if (sg != nullptr) {
+      *sg = StepSignal{this, ln, ln->seq};  // seq is written by this thread only
+      if (cudaLaunchHostFunc(ln->st, step_done_host_fn, sg) != cudaSuccess) {
+        cudaGetLastError();
+        delete sg;
+      }
+    }
+  }
   return e;
 }
 
@@ -418,10 +472,10 @@ void sk_server::scheduler() {
       bool busy = false;
       for (const Lane& l : lanes) busy |= l.busy;
       if (busy) {
-        // a step is in flight: poll its event without holding the lock
-        lk.unlock();
-        std::this_thread::yield();
-        lk.lock();
+        // a step is in flight: sleep until its host function (or new work)
+        // wakes the scheduler; the timeout only bounds the wait should the
+        // host function not have been enqueued
+        work_cv.wait_for(lk, std::chrono::milliseconds(2));
       } else {
         work_cv.wait(lk);
       }
@@ -495,6 +549,10 @@ void sk_server::scheduler() {
       lk.lock();
     }
   retire_lanes(lk);
+  // the completion host functions take mu: wait for them without it
+  lk.unlock();
+  for (Lane& l : lanes) cudaStreamSynchronize(l.st);
+  lk.lock();
   cudaStreamSynchronize(copy_st);
   done_cv.notify_all();
 }

@@ -62,8 +62,10 @@ template <bool LEFT>
 __global__ void __launch_bounds__(TPB) k_sketch_fp32_simt(SimtParams p) {
   __shared__ __align__(16) float Xs[BL][BP + PAD];
   __shared__ __align__(16) float Ws[BL][BQ + PAD];
-  const int64_t q0 = (int64_t)blockIdx.x * BQ;
-  const int64_t p0 = (int64_t)blockIdx.y * BP;
+  // the tiles along the long side (n of the left sketch, m of the right) run
+  // along grid x, whose extent is not limited to 65535
+  const int64_t q0 = (int64_t)(LEFT ? blockIdx.x : blockIdx.y) * BQ;
+  const int64_t p0 = (int64_t)(LEFT ? blockIdx.y : blockIdx.x) * BP;
   const int64_t lbeg = (int64_t)blockIdx.z * p.chunk;
   const int64_t lend = min(p.L, lbeg + p.chunk);
   const int tq = threadIdx.x % 16;
@@ -274,7 +276,10 @@ cudaError_t simt_sketch(const sk_sketch* h, const GemmShape& s, const float* A, 
     p.out = Y;
     p.ldo = ldy;
   }
-  dim3 grid((unsigned)((s.Q + BQ - 1) / BQ), (unsigned)((s.P + BP - 1) / BP), (unsigned)splits);
+  // grid x: tiles of the long side (n or m); grid y: tiles of k, at most
+  // 65535 (k <= 8,388,480 in this form; a larger k fails the launch)
+  const unsigned tq = (unsigned)((s.Q + BQ - 1) / BQ), tp = (unsigned)((s.P + BP - 1) / BP);
+  dim3 grid(s.left ? tq : tp, s.left ? tp : tq, (unsigned)splits);
   prof_mark(h->prof_start, st);
   if (s.left)
     k_sketch_fp32_simt<true><<<grid, TPB, 0, st>>>(p);
@@ -313,8 +318,6 @@ cudaError_t materialize(const sk_sketch* h, int64_t row0, int64_t col0, int64_t 
 // partials of the FP32 left sketch live in a fixed array compiled into the
 // library instead of in an allocated workspace.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace sk {
 namespace {
 
@@ -323,26 +326,16 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) float g_static_scratch[kStaticScratchBytes / sizeof(float)];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_scratch_mu;
-void* g_static_scratch_addr[kMaxDevices];
-
 // Device address of g_static_scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and cached.
+// cudaGetSymbolAddress, with the device current, on every call: a cached
+// address would outlive a cudaDeviceReset, after which the library's device
+// code (and this array) is loaded again, possibly elsewhere.
 cudaError_t static_scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
-  if (g_static_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_scratch_addr[dev] = p;
-  }
-  *out = g_static_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -365,9 +358,5 @@ extern "C" sk_status sk_apply_left_noalloc(sk_handle h, const float* A, int64_t 
   if (e == cudaSuccess)
     e = sk::simt_sketch(h, s, A, lda, Y, ldy, scratch, sk::kStaticScratchBytes,
                         static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return SK_ECUDA;
-  }
-  return SK_OK;
+  return sk::status_from_cuda(e);
 }

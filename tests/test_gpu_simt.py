@@ -173,3 +173,24 @@ def test_invalid_arguments(P):
             assert e.value.status == 1
     finally:
         P.sk_destroy(h)
+
+
+def test_right_fp32_beyond_65535_row_tiles(P, orc):
+    """A right sketch whose m needs more than 65535 tiles of 128 rows (the
+    long side runs along the launch grid's x extent): sampled rows of Y,
+    including the last tile's, against the oracle."""
+    m, n, k, seed = 65536 * 128 + 300, 6, 24, 13
+    A = torch.randn((m, n), generator=torch.Generator().manual_seed(seed))
+    Y = torch.full((m, k), float("nan"), dtype=torch.float32, device="cuda")
+    h = P.sk_create(seed, G, k)
+    try:
+        P.sk_apply_right(h, A.cuda(), m, n, n, Y, k)
+        assert P.sk_stream_status(h) == 0
+    finally:
+        P.sk_destroy(h)
+    rows = np.unique(np.r_[np.arange(0, 8), np.linspace(0, m - 1, 200).astype(np.int64),
+                           np.arange(m - 300, m)])
+    got = Y[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ref = orc.apply_right(seed, G, 0, k, A.numpy(), rows=rows)
+    assert np.all(np.isfinite(got))
+    assert rel_frob(got, ref) <= TOL

@@ -72,3 +72,47 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
                                              64, None) == N.SK_EUNSUPPORTED
     finally:
         N.sk_destroy(h)
+
+
+def test_noalloc_cuda_error_is_reported_like_every_other_entry_point():
+    """A CUDA failure inside the allocation-free call comes back as SK_ECUDA
+    with sk_last_cuda_error describing it, as for the allocating call.  The
+    failure used is one CUDA detects on the host before anything runs: in the
+    FP32 form a sketch size k above 65535 tiles of 128 rows is a launch grid
+    CUDA refuses."""
+    require_gpu()
+    from paper_2603_20966_gb300 import _native as N
+    L = N.lib()
+    k, m, n = 65536 * 128, 32, 4
+    h = N.sk_create(3, N.SK_GAUSSIAN, k)
+    try:
+        A = torch.zeros((m, n), device="cuda")
+        Y = torch.zeros((k, n), device="cuda")
+        stream = torch.cuda.current_stream()
+        assert N.sk_workspace_size(h, 0, m, n) == 0  # within the array's limit
+        st = L.sk_apply_left_noalloc(h, A.data_ptr(), m, n, n, Y.data_ptr(), n,
+                                     stream.cuda_stream)
+        assert st == N.SK_ECUDA
+        msg = L.sk_last_cuda_error().decode()
+        assert msg != "no error" and "configuration" in msg
+        # the allocating entry point reports the same failure the same way
+        assert L.sk_apply_left(h, A.data_ptr(), m, n, n, Y.data_ptr(), n,
+                               stream.cuda_stream) == N.SK_ECUDA
+        assert L.sk_last_cuda_error().decode() == msg
+        # the error is not sticky: the context still runs work, and a later
+        # successful call leaves the description of the last failure in place
+        k2, m2 = 64, 4096
+        h2 = N.sk_create(5, N.SK_GAUSSIAN, k2)
+        try:
+            A2 = torch.randn((m2, n), device="cuda")
+            Y2 = torch.full((k2, n), float("nan"), device="cuda")
+            Y2_ref = torch.empty((k2, n), device="cuda")
+            N.sk_apply_left(h2, A2, m2, n, n, Y2_ref, n, stream)
+            assert _raw_noalloc(N, h2, A2, m2, n, Y2, stream) == N.SK_OK
+            assert N.sk_stream_status(h2, stream) == N.SK_OK
+            assert L.sk_last_cuda_error().decode() == msg
+            assert rel_frob(Y2.cpu().numpy(), Y2_ref.cpu().numpy()) <= TOL
+        finally:
+            N.sk_destroy(h2)
+    finally:
+        N.sk_destroy(h)
