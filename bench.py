@@ -482,10 +482,16 @@ def _serve_stream(P, srv, reqs, hs, src_ptr, src_ld, fetch=None):
         if errors or not done.is_set():
             raise RuntimeError(f"serving e2e leg failed: {errors or 'timeout'}")
     else:
+        last, t_last = -1, time.perf_counter()
         while time.perf_counter() < deadline:
             s = P.sk_server_stats_get(srv)
-            if s["completed"] + s["failed"] >= len(reqs):
+            done_n = s["completed"] + s["failed"]
+            if done_n >= len(reqs):
                 break
+            if done_n != last:
+                last, t_last = done_n, time.perf_counter()
+            elif time.perf_counter() - t_last > 60.0:
+                raise RuntimeError(f"serving stream made no progress for 60 s: {s}")
             time.sleep(0.002)
     wall = time.perf_counter() - t0
     s = P.sk_server_stats_get(srv)

@@ -142,19 +142,17 @@ __device__ __forceinline__ float2 div_x2(float2 a, float2 b) {
 // d = w - g^2 (one FMA): g + d h, rounded once.  The same exhaustive check
 // (every radicand, every seed within 6 ulp; the hardware approximation is
 // within 2^-22.9 relative) finds every root equal to the IEEE one.  The seed
-// is infinite at w = 0, whose root is w itself.
+// is taken at max(w, 1e-30), which changes nothing for w >= 2^-23 and keeps it
+// finite at w = -0 (u1 = 1), where every step then yields -0, the root.
 __device__ __forceinline__ float2 sqrt_x2(float2 w) {
-  const float2 y = f2(rsqrt_approx(w.x), rsqrt_approx(w.y));
+  const float2 y = f2(rsqrt_approx(fmaxf(w.x, 1e-30f)), rsqrt_approx(fmaxf(w.y, 1e-30f)));
   float2 g = __fmul2_rn(w, y);
   float2 h = __fmul2_rn(f2(0.5f, 0.5f), y);
   const float2 t = __ffma2_rn(neg2(g), h, f2(0.5f, 0.5f));
   g = __ffma2_rn(g, t, g);
   h = __ffma2_rn(h, t, h);
   const float2 d = __ffma2_rn(neg2(g), g, w);
-  float2 s = __ffma2_rn(d, h, g);
-  if (w.x == 0.0f) s.x = w.x;
-  if (w.y == 0.0f) s.y = w.y;
-  return s;
+  return __ffma2_rn(d, h, g);
 }
 
 // ln x for x in (0, 1] (normal): x = 2^e f, f folded into [sqrt(1/2), sqrt 2],
@@ -162,17 +160,18 @@ __device__ __forceinline__ float2 sqrt_x2(float2 w) {
 // coefficients 2/3, 2/5, 2/7, 2/9; ln x = e ln2_hi + (e ln2_lo + ln f).
 __device__ __forceinline__ float2 ln01_x2(float2 x) {
   const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
-  // biased exponent E (plus one when f is folded down); e = E - 127
-  uint32_t m0 = b0 & 0x007fffffu, m1 = b1 & 0x007fffffu;
-  const uint32_t up0 = m0 > 0x003504f3u ? 1u : 0u, up1 = m1 > 0x003504f3u ? 1u : 0u;
-  m0 |= up0 ? 0x3f000000u : 0x3f800000u;
-  m1 |= up1 ? 0x3f000000u : 0x3f800000u;
+  // Fold and split by one integer add: with m the mantissa bits, b + 0x4afb0c
+  // carries into the exponent field exactly when m > 0x3504f3 (the fold), so
+  // its exponent field is E (plus one when folded) and its mantissa field
+  // plus 0x3f3504f4 is m with the exponent of 1 (or of 1/2 when folded).
+  const uint32_t i0 = b0 + 0x004afb0cu, i1 = b1 + 0x004afb0cu;
   // e as a float without a conversion: 0x4B000000 + E is the float 2^23 + E
   // (E < 2^8), and subtracting 2^23 + 127 is exact
-  const float2 eb = f2(__uint_as_float(0x4B000000u + (b0 >> 23) + up0),
-                       __uint_as_float(0x4B000000u + (b1 >> 23) + up1));
+  const float2 eb = f2(__uint_as_float(0x4B000000u + (i0 >> 23)),
+                       __uint_as_float(0x4B000000u + (i1 >> 23)));
   const float2 ef = __fadd2_rn(eb, f2(-8388735.0f, -8388735.0f));
-  const float2 f = f2(__uint_as_float(m0), __uint_as_float(m1));
+  const float2 f = f2(__uint_as_float((i0 & 0x007fffffu) + 0x3f3504f4u),
+                      __uint_as_float((i1 & 0x007fffffu) + 0x3f3504f4u));
   const float2 num = __fadd2_rn(f, f2(-1.0f, -1.0f));
   const float2 den = __fadd2_rn(f, f2(1.0f, 1.0f));
   const float2 sv = div_x2(num, den);

@@ -7,7 +7,7 @@
 // Request state lives in one map guarded by one mutex; the scheduler drops
 // the mutex while it issues CUDA work and while it sleeps.  While a step is
 // in flight the scheduler sleeps: a host function enqueued behind each step
-// wakes it when the step has finished.
+// records the completion time and wakes it (without taking the mutex).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -153,10 +153,13 @@ struct Lane {
   bool busy = false;
   std::vector<int64_t> tickets;
   // completion signal of the step in flight: a host function enqueued after
-  // the step records when it ran and wakes the scheduler (under mu)
-  uint64_t seq = 0;  // steps launched on this lane
-  bool signalled = false;
-  Clock::time_point t_signal;
+  // the step records when it ran and wakes the scheduler.  It takes no lock
+  // (a thread holding mu may be inside a CUDA call that waits for the CUDA
+  // thread running host functions), so these fields are atomics.
+  std::atomic<uint64_t> seq{0};            // steps launched on this lane
+  std::atomic<uint64_t> signalled_seq{0};  // the step whose host function ran
+  std::atomic<int64_t> t_signal_ns{0};     // when it ran (steady clock)
+  Clock::time_point t_launch;              // when the step was taken (under mu)
 };
 
 }  // namespace
@@ -169,6 +172,13 @@ struct sk_server {
   Lane lanes[kLanes];
   cudaStream_t copy_st = nullptr;
   cudaEvent_t copy_ev = nullptr;
+  // GPU-clock reference for completion times: ref_ev completed at about
+  // host time ref_host (recorded on an idle stream and synchronised on), so a
+  // step's Y-ready event maps to ref_host + elapsed(ref_ev, done)
+  cudaEvent_t ref_ev = nullptr;
+  Clock::time_point ref_host;
+  bool ref_valid = false;
+  void calibrate_clock();
   bool copy_recorded = false;
   std::vector<cudaEvent_t> free_events;  // submission events not in use (under mu)
   std::vector<cudaEvent_t> all_events;
@@ -218,13 +228,12 @@ struct StepSignal {
 // step is in flight.
 void CUDART_CB step_done_host_fn(void* p) {
   StepSignal* sg = static_cast<StepSignal*>(p);
-  {
-    std::lock_guard<std::mutex> g(sg->s->mu);
-    if (sg->ln->seq == sg->seq) {
-      sg->ln->signalled = true;
-      sg->ln->t_signal = Clock::now();
-    }
+  if (sg->ln->seq.load() == sg->seq) {
+    sg->ln->t_signal_ns.store(Clock::now().time_since_epoch().count());
+    sg->ln->signalled_seq.store(sg->seq);
   }
+  // no lock: a wake-up that slips in between the scheduler's last look at
+  // the signals and its wait is caught by the wait's short timeout
   sg->s->work_cv.notify_one();
   delete sg;
 }
@@ -262,6 +271,21 @@ cudaError_t sk_server::issue_copy(const AdmitCopy& c) {
                                                                       c.ldd, c.m, c.n);
   sk::count_launches(1);
   return cudaGetLastError();
+}
+
+// Record ref_ev on the idle copy stream and note when it completed.  Called
+// without mu while no step is in flight (at creation and then at most once a
+// second when the lanes are idle), which bounds the drift between the GPU
+// and host clocks to what accumulates in about a second.
+void sk_server::calibrate_clock() {
+  if (cudaEventRecord(ref_ev, copy_st) != cudaSuccess ||
+      cudaEventSynchronize(ref_ev) != cudaSuccess) {
+    cudaGetLastError();
+    ref_valid = false;
+    return;
+  }
+  ref_host = Clock::now();
+  ref_valid = true;
 }
 
 void sk_server::free_work(Request& r) {
@@ -308,9 +332,21 @@ bool sk_server::retire_lanes(std::unique_lock<std::mutex>&) {
     if (!ln.busy) continue;
     const cudaError_t q = cudaEventQuery(ln.done);
     if (q == cudaErrorNotReady) continue;
-    // the step's host function ran when it finished (it may still be on its
-    // way if the event was seen first)
-    const Clock::time_point now = ln.signalled ? ln.t_signal : Clock::now();
+    // a request's latency ends when its step's Y-ready event completed: the
+    // event's GPU time mapped to the host clock (or, without a reference,
+    // when the step's host function ran, or now)
+    const Clock::time_point seen = Clock::now();
+    Clock::time_point now =
+        ln.signalled_seq.load() == ln.seq.load()
+            ? Clock::time_point(Clock::duration(ln.t_signal_ns.load()))
+            : seen;
+    float ev_ms = 0.0f;
+    if (q == cudaSuccess && ref_valid && cudaEventElapsedTime(&ev_ms, ref_ev, ln.done) == cudaSuccess)
+      now = std::max(ln.t_launch,
+                     std::min(seen, ref_host + std::chrono::duration_cast<Clock::duration>(
+                                                   std::chrono::duration<double, std::milli>(ev_ms))));
+    else
+      cudaGetLastError();
     sk_status err = SK_OK;
     if (q != cudaSuccess) {
       err = sk::status_from_cuda(q);
@@ -392,8 +428,8 @@ std::vector<StepItem> sk_server::take_step_locked(Lane* ln) {
   }
   admitted.erase(admitted.begin(), admitted.begin() + take);
   ln->busy = true;
-  ++ln->seq;
-  ln->signalled = false;
+  ln->t_launch = now;
+  ln->seq.fetch_add(1);
   ++steps;
   max_step = std::max<int64_t>(max_step, static_cast<int64_t>(take));
   return items;
@@ -441,7 +477,7 @@ cudaError_t sk_server::launch_items(Lane* ln, const std::vector<StepItem>& items
     // enqueued the scheduler still polls the event, at a slower cadence
     StepSignal* sg = new (std::nothrow) StepSignal;
     if (sg != nullptr) {
-      *sg = StepSignal{this, ln, ln->seq};  // seq is written by this thread only
+      *sg = StepSignal{this, ln, ln->seq.load()};  // seq is written by this thread only
       if (cudaLaunchHostFunc(ln->st, step_done_host_fn, sg) != cudaSuccess) {
         cudaGetLastError();
         delete sg;
@@ -473,11 +509,22 @@ void sk_server::scheduler() {
       for (const Lane& l : lanes) busy |= l.busy;
       if (busy) {
         // a step is in flight: sleep until its host function (or new work)
-        // wakes the scheduler; the timeout only bounds the wait should the
-        // host function not have been enqueued
-        work_cv.wait_for(lk, std::chrono::milliseconds(2));
+        // wakes the scheduler, unless one has signalled already; the short
+        // timeout bounds the cost of a wake-up that arrived between this
+        // check and the wait (the host function takes no lock)
+        bool signalled = false;
+        for (const Lane& l : lanes)
+          signalled |= l.busy && l.signalled_seq.load() == l.seq.load();
+        if (!signalled) work_cv.wait_for(lk, std::chrono::microseconds(200));
       } else {
-        work_cv.wait(lk);
+        // idle: refresh the clock reference if it is a second old
+        if (!ref_valid || Clock::now() - ref_host > std::chrono::seconds(1)) {
+          lk.unlock();
+          calibrate_clock();
+          lk.lock();
+          continue;
+        }
+        work_cv.wait_for(lk, std::chrono::seconds(1));
       }
       continue;
     }
@@ -570,6 +617,7 @@ void destroy_resources(sk_server* s) {
     if (l.arena.h_stage) cudaFreeHost(l.arena.h_stage);
   }
   if (s->copy_ev) cudaEventDestroy(s->copy_ev);
+  if (s->ref_ev) cudaEventDestroy(s->ref_ev);
   if (s->copy_st) cudaStreamDestroy(s->copy_st);
   for (cudaEvent_t ev : s->all_events) cudaEventDestroy(ev);
   s->pool.destroy();
@@ -607,7 +655,7 @@ sk_status sk_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, sk_serv
   if (e == cudaSuccess) e = s->pool.init(hbm_budget_bytes);
   for (Lane& l : s->lanes) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.done, cudaEventDefault);  // timed
     if (e == cudaSuccess)
       e = cudaHostAlloc(reinterpret_cast<void**>(&l.h_status), sizeof(int) * 4,
                         cudaHostAllocDefault);
@@ -619,6 +667,8 @@ sk_status sk_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, sk_serv
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ref_ev, cudaEventDefault);
+  if (e == cudaSuccess) s->calibrate_clock();
   if (e != cudaSuccess) {
     const sk_status st = sk::status_from_cuda(e);
     destroy_resources(s);

@@ -169,6 +169,10 @@ struct LeftSched {
   int nitems;
   int* status;
   uint64_t timeout_ns;
+  // failure-injection hook of the tests, -1 otherwise: the TMA producer
+  // issues no copy for this stage (counted over each CTA's or pair's run),
+  // so the waits that depend on it give up after timeout_ns
+  long long stall_stage;
   PhiloxRoundKeys rk;  // round keys of problem 0 (read when a launch has one distribution)
 };
 
@@ -531,6 +535,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int so = g % C::NSO;
           // the MMAs that read this slot last time have completed
           if (g >= C::NSO && !mbar_wait(empty_o(so), ((g / C::NSO) & 1) ^ 1, ab, 0x13, g)) break;
+          if (g == sc.stall_stage) continue;  // injected stall: this stage never lands
           mbar_arrive_expect_tx(full_b(so), tx);
           const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * LK);
           tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
@@ -1748,7 +1753,8 @@ void pack_sched(HostSched* hs) {
   memcpy(hs->blob.data() + hs->off_items, hs->items.data(), ib);
 }
 
-LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
+LeftSched device_sched(const HostSched& hs, void* dbuf, int* status,
+                       uint64_t timeout_ns = kDefaultWaitLimitNs, long long stall_stage = -1) {
   LeftSched sc;
   uint8_t* b = static_cast<uint8_t*>(dbuf);
   sc.probs = reinterpret_cast<const LeftProblem*>(b);
@@ -1756,7 +1762,8 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status) {
   sc.claim = reinterpret_cast<int*>(b + hs.off_claim);
   sc.nitems = static_cast<int>(hs.items.size());
   sc.status = status;
-  sc.timeout_ns = 2000000000ull;  // 2 s per wait: far beyond any healthy stage
+  sc.timeout_ns = timeout_ns;
+  sc.stall_stage = stall_stage;
   sc.rk = round_keys(hs.probs.empty() ? PhiloxKey{0u, 0u} : hs.probs[0].key);
   return sc;
 }
@@ -2034,7 +2041,7 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   p.tmem_cols = pl.tmem_cols;
   p.rk = round_keys(make_key(h->seed));
   p.status = h->d_status;
-  p.timeout_ns = 2000000000ull;
+  p.timeout_ns = h->wait_limit_ns;
   const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
   p.part = static_cast<float*>(ws);
@@ -2112,7 +2119,7 @@ cudaError_t q8_sketch_right_quantized(const sk_sketch* h, const GemmShape& s, co
   p.tmem_cols = pl.tmem_cols;
   p.rk = round_keys(make_key(h->seed));
   p.status = h->d_status;
-  p.timeout_ns = 2000000000ull;
+  p.timeout_ns = h->wait_limit_ns;
   dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
             static_cast<unsigned>(pl.splits));
   prof_mark(h->prof_start, st);
@@ -2180,7 +2187,8 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
     if (e != cudaSuccess) return e;
     memcpy(hm->sched_key, key, sizeof(key));
   }
-  const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status);
+  const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status, h->wait_limit_ns,
+                                    h->stall_stage);
   const int64_t nunits = hs.units;
   // the measurement hook brackets both passes: split of A, then the sketch
   prof_mark(h->prof_start, st);

@@ -70,6 +70,18 @@ struct Abort {
 // queue slot free, 9 = work item published (reported by the reading role's
 // first site code in use, 0x19).
 
+// Record a give-up: raise the CTA's abort flag and, if this is the launch's
+// first, SK_ETIMEOUT with the site, stage and CTA in the status words.
+__device__ __forceinline__ void give_up(const Abort& ab, int site, int stage) {
+  *ab.flag = 1;
+  if (atomicCAS(ab.status, 0, 4) == 0) {  // first give-up of the launch records its site
+    ab.status[1] = site;
+    ab.status[2] = stage;
+    ab.status[3] = static_cast<int>(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y *
+                                                              blockIdx.z));
+  }
+}
+
 // Wait until the phase with `parity` of barrier `bar` completed.  Gives up
 // (returns false) when another thread of the CTA raised the abort flag or when
 // `limit_ns` elapsed, in which case it raises the flag and records
@@ -88,13 +100,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const A
     if ((++it & 63u) == 0) {
       if (*ab.flag) return false;
       if (globaltimer() - t0 > ab.limit_ns) {
-        *ab.flag = 1;
-        if (atomicCAS(ab.status, 0, 4) == 0) {  // first give-up of the launch records its site
-          ab.status[1] = site;
-          ab.status[2] = stage;
-          ab.status[3] = static_cast<int>(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y *
-                                                                    blockIdx.z));
-        }
+        give_up(ab, site, stage);
         return false;
       }
     }

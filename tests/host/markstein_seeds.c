@@ -39,9 +39,7 @@ static float sqrt_seq(float w, float y) {
   g = fmaf(g, t, g);
   h = fmaf(h, t, h);
   float d = fmaf(-g, g, w);
-  float s = fmaf(d, h, g);
-  if (w == 0.0f) s = w;
-  return s;
+  return fmaf(d, h, g);
 }
 
 int main(void) {
@@ -54,10 +52,11 @@ int main(void) {
     float q_ieee = a / b, y_rn = 1.0f / b;
     float w = -2.0f * orc_ln1(u1);
     float s_ieee = sqrtf(w);
-    float ry_rn = (float)(1.0 / sqrt((double)w)); /* inf at w = 0 */
+    /* the device takes its seed at max(w, 1e-30): finite at w = -0 (u1 = 1) */
+    float ry_rn = (float)(1.0 / sqrt((double)fmaxf(w, 1e-30f)));
     for (int k = -SEED_ULPS; k <= SEED_ULPS; ++k) {
       if (f2u(div_seq(a, b, u2f(f2u(y_rn) + k))) != f2u(q_ieee)) ++bad_div;
-      float ys = w == 0.0f ? ry_rn : u2f(f2u(ry_rn) + k);
+      float ys = u2f(f2u(ry_rn) + k);
       if (f2u(sqrt_seq(w, ys)) != f2u(s_ieee)) ++bad_sqrt;
       ++cases;
     }
