@@ -412,8 +412,8 @@ sk_status sk_server_destroy(sk_server_handle s);
  * [1] where the first bounded wait that gave up was waiting (role * 16 +
  * barrier: roles 1 TMA producer, 2 MMA issuer, 3 epilogue, 4 worker;
  * barriers 0 staging full, 1 staging empty, 2 operand full, 3 operand empty,
- * 4 accumulator full, 5 accumulator empty, 8 work-queue slot free, 9 work
- * item published), [2] the pipeline stage (or
+ * 4 accumulator full, 5 accumulator empty, 6 S rows received from another
+ * CTA, 8 work-queue slot free, 9 work item published), [2] the pipeline stage (or
  * accumulation chain) it was waiting for, [3] the linear index of its CTA.
  * Words 1-3 are meaningful only when word 0 is SK_ETIMEOUT. */
 sk_status sk_debug_status(sk_handle h, void* stream, int32_t out[4]);

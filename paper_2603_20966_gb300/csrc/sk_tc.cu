@@ -820,7 +820,8 @@ struct CfgR {
   static constexpr uint32_t OFF_ALO = OFF_AHI + NSO * OPA;
   static constexpr uint32_t OFF_S = OFF_ALO + NSO * OPA;
   static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
-  static constexpr uint32_t NUM_BARS = 2 * NSF + 2 * NSO + 3;
+  // + per operand slot, the S rows received from the partner CTA
+  static constexpr uint32_t NUM_BARS = 2 * NSF + 3 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
@@ -851,7 +852,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
   auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
   auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 2 * C::NSO);
+  // s_recv: the S rows the partner CTA copies into operand slot i have landed
+  auto s_recv = [&](int i) { return bar0 + 8u * (2 * C::NSF + 2 * C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 3 * C::NSO);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
@@ -859,10 +862,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_ctarank() & 1u;  // 0 = even CTA (MMA issuer)
+  // a cluster holds two CTA pairs (cluster ranks 0-1 and 2-3) with the same
+  // k rows and the same range of n on consecutive rows of m; the two CTAs of
+  // equal rank in the two pairs hold the same rows of the S tile, and each
+  // generates half of them and copies that half into its partner
+  const uint32_t cr = cluster_ctarank();
+  const uint32_t rank = cr & 1u;  // 0 = even CTA of the pair (MMA issuer)
+  const uint32_t pairi = cr >> 1;
+  const uint32_t lead_rank = cr & ~1u;          // the pair's even CTA
+  const uint32_t partner = cr ^ 2u;             // same rank, other pair
+  const uint32_t partner_lead = partner & ~1u;  // the other pair's even CTA
   const bool leader = rank == 0;
   const int nq = p.nq;
-  const int gh = nq / 2;                                       // S rows this CTA generates
+  const int gh = nq / 2;                                       // S rows this CTA holds
+  const int gq = gh / 2;                                       // ... and generates
+  const int gbase = static_cast<int>(pairi) * gq;              // from this row of them
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * C::ROWS;  // this CTA's rows of A
   const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nq;       // the pair's k rows
   const int64_t g0 = q0 + static_cast<int64_t>(rank) * gh;        // this CTA's S rows
@@ -877,8 +891,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(empty_f(i), C::GROUP_WARPS);
     }
     for (int i = 0; i < C::NSO; ++i) {
-      mbar_init(full_o(i), C::GROUP_WARPS * 2);
-      mbar_init(empty_o(i), 1);
+      mbar_init(full_o(i), C::GROUP_WARPS * 2);  // one worker group of each CTA of the pair
+      mbar_init(empty_o(i), 2);  // the MMAs of both pairs read what this CTA wrote
+      mbar_init(s_recv(i), 1);   // the receiving group's expect-tx, plus the copy's bytes
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_EPI_WARPS * 2);
@@ -897,8 +912,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const Abort ab{abort_flag, p.status, p.timeout_ns};
-  const uint32_t lead_full_o = mapa_shared(full_o(0), 0u);
-  const uint32_t lead_acc_empty = mapa_shared(acc_empty, 0u);
+  const uint32_t lead_full_o = mapa_shared(full_o(0), lead_rank);
+  const uint32_t partner_s_recv = mapa_shared(s_recv(0), partner);
+  const uint32_t partner_s = mapa_shared(sbase + C::OFF_S, partner);
+  const uint32_t lead_acc_empty = mapa_shared(acc_empty, lead_rank);
+  const uint16_t pair_mask = static_cast<uint16_t>(3u << (2u * pairi));
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
@@ -939,8 +957,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           (in_chain > 0 || pass > 0) ? 1u : 0u);
           }
         }
-        mma_commit_pair_both(empty_o(so));
-        if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit_pair_both(acc_full);
+        mma_commit_pair_mask(empty_o(so), 0xF);  // all four CTAs wrote into the slot
+        if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit_pair_mask(acc_full, pair_mask);
       }
       mma_commit_pair(drain_bar);
       drain_wait(drain_bar, 0, 200000000ull);
@@ -1001,6 +1019,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- workers: this CTA's half of the S tile, and its 256 rows of A ----
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
     const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
+    const bool gfirst = wt < 32;  // the group's first warp does its copies and expect-tx
+    // the rows this CTA generates: whole 8-row groups, contiguous in the K-major
+    // layout (256 B per group), copied as one block
+    const uint32_t s_off = static_cast<uint32_t>(gbase / 8) * 256u;
+    const uint32_t s_bytes = static_cast<uint32_t>(gq) * 32u;
     constexpr int RAD_IT = (2 * 128 + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
     uint32_t cached_blk[RAD_IT];
     uint4 words[RAD_IT];
@@ -1012,17 +1035,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int s = grp; s < nsteps; s += C::NGROUPS) {
       const int sf = s % C::NSF;
       const int so = s % C::NSO;
+      // both pairs' MMAs have read what this CTA wrote into slot `so` (here
+      // and in its partner) last time
       bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
+      // the partner's half of this CTA's S rows will land here
+      if (gfirst && lane == 0) mbar_arrive_expect_tx(s_recv(so), s_bytes);
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
       if (DIST == kRademacher) {
 #pragma unroll
         for (int it = 0; it < RAD_IT; ++it) {
           const int t = wt + it * C::GROUP_THREADS;
-          if (t >= 2 * gh) break;
-          const uint32_t r = static_cast<uint32_t>(t % gh);
-          const uint32_t hh = static_cast<uint32_t>(t / gh);
+          if (t >= 2 * gq) break;
+          const uint32_t r = static_cast<uint32_t>(gbase + t % gq);
+          const uint32_t hh = static_cast<uint32_t>(t / gq);
           const int64_t grow = g0 + r;
           const int64_t c0 = cbase + 8 * hh;
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -1045,20 +1072,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
         }
       } else {
-        // thread wt owns quad qd of rows rb + RSTEP it (4 quads per row)
+        // thread wt owns quad qd of rows gbase + rb + RSTEP it (4 quads per row)
         constexpr int RSTEP = C::GROUP_THREADS / 4;
-        constexpr int GEN_IT = 128 / RSTEP;
-        static_assert(RSTEP % 8 == 0, "row passes of the worker group");
+        constexpr int GEN_IT = 64 / RSTEP;  // rows of the generated half: gq <= 64
+        static_assert(RSTEP % 8 == 0 && GEN_IT >= 1, "row passes of the worker group");
         const uint32_t qd = static_cast<uint32_t>(wt) & 3u;
         const uint32_t rb = static_cast<uint32_t>(wt) >> 2;
-        // kmaj_off(rb + RSTEP it, qd / 2) = off0 + 32 RSTEP it
-        const uint32_t off0 = kmaj_off(rb, qd >> 1) + (qd & 1u) * 8u;
         const bool cv = cbase + 4 * qd < lend;
         const uint32_t j = static_cast<uint32_t>(cbase >> 2) + qd;  // Philox block
 #pragma unroll 2
         for (int it = 0; it < GEN_IT; ++it) {
-          const uint32_t r = rb + static_cast<uint32_t>(RSTEP * it);
-          if (r >= static_cast<uint32_t>(gh)) break;
+          const uint32_t rr = rb + static_cast<uint32_t>(RSTEP * it);
+          if (rr >= static_cast<uint32_t>(gq)) break;
+          const uint32_t r = static_cast<uint32_t>(gbase) + rr;
           const int64_t grow = g0 + r;
           uint2 v = make_uint2(0u, 0u);
           if (grow < p.Q && cv) {
@@ -1067,9 +1093,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                  : gaussian4(p.rk, static_cast<uint32_t>(grow), j, 0u);
             v = make_uint2(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w));
           }
-          *reinterpret_cast<uint2*>(sdst + off0 + static_cast<uint32_t>(it * RSTEP * 32)) = v;
+          const uint32_t off = kmaj_off(r, qd >> 1) + (qd & 1u) * 8u;
+          *reinterpret_cast<uint2*>(sdst + off) = v;
         }
       }
+      // the group's rows are written: copy them into the partner (async
+      // proxy, completing on its s_recv barrier)
+      fence_proxy_async_smem();
+      named_bar_sync(1u + static_cast<uint32_t>(grp), C::GROUP_THREADS);
+      if (gfirst && lane == 0)
+        bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + s_off,
+                             smem_u32(sdst) + s_off, s_bytes, partner_s_recv + 8u * so);
       ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
@@ -1099,8 +1133,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         *reinterpret_cast<uint4*>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      // the S half and the A operands are in this CTA's own shared memory
+      // the S half and the A operands are in this CTA's own shared memory;
+      // the group's first warp certifies the partner's rows too
       fence_proxy_async_smem();
+      ok = !gfirst || mbar_wait(s_recv(so), (s / C::NSO) & 1, ab, 0x46, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
       __syncwarp();
       if (lane == 0) {
         mbar_arrive_cluster(lead_full_o + 8u * so);
@@ -1558,15 +1595,18 @@ cudaError_t set_smem_attr() {
   return e;
 }
 
+// cluster_x: CTAs per cluster along x (a CTA pair must be adjacent in x; the
+// BF16 right sketch runs clusters of two pairs)
 template <bool PAIR>
-void fill_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, dim3 grid, cudaStream_t st) {
+void fill_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, dim3 grid, cudaStream_t st,
+                 unsigned cluster_x = PAIR ? 2 : 1) {
   *cfg = cudaLaunchConfig_t{};
   cfg->gridDim = grid;
   cfg->blockDim = dim3(NTHREADS, 1, 1);
   cfg->dynamicSmemBytes = Cfg<PAIR>::SMEM;
   cfg->stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = PAIR ? 2 : 1;  // a CTA pair must be adjacent in x
+  attr[0].val.clusterDim.x = cluster_x;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg->attrs = attr;
@@ -1870,16 +1910,25 @@ struct Plan {
   int64_t chunk;
 };
 
-// Right sketch: pairs of CTAs own 512 rows of m and nq <= 256 rows of k; the
-// split count keeps the partials (splits x m x k floats) to a few hundred MB.
-Plan plan_right(const GemmShape& s) {
+// CTAs of the BF16 right kernel that can be resident at once in clusters of
+// two pairs (a cluster must fit in one GPC), or -1.
+int64_t quad_slots();
+
+// Right sketch: pairs of CTAs own 512 rows of m and nq <= 256 rows of k,
+// `cluster` CTAs (two pairs for the BF16 kernel, one for FP8) are adjacent in
+// x; the split count keeps the partials (splits x m x k floats) to a few
+// hundred MB.
+Plan plan_right(const GemmShape& s, int cluster = 4) {
   Plan pl;
-  pl.nt = s.Q > 256 ? 256 : static_cast<int>((s.Q + 15) / 16 * 16);
+  // k rows per pair tile: a multiple of 32, so that each CTA of a pair holds
+  // whole 8-row groups of S in each half it generates and receives
+  pl.nt = s.Q > 256 ? 256 : static_cast<int>((s.Q + 31) / 32 * 32);
   pl.tmem_cols = 32;
   while (pl.tmem_cols < 2 * pl.nt) pl.tmem_cols *= 2;
-  pl.tiles_p = (s.P + 2 * CfgR::ROWS - 1) / (2 * CfgR::ROWS) * 2;  // CTAs along m
+  const int64_t rows = static_cast<int64_t>(cluster) * CfgR::ROWS;  // rows of m per cluster
+  pl.tiles_p = (s.P + rows - 1) / rows * cluster;                  // CTAs along m
   pl.tiles_q = (s.Q + pl.nt - 1) / pl.nt;
-  int64_t slots = pair_slots();
+  int64_t slots = cluster == 4 ? quad_slots() : pair_slots();
   if (slots <= 0) slots = num_sms_tc();
   const int64_t tiles = pl.tiles_p * pl.tiles_q;
   const int64_t steps_total = (s.L + BK - 1) / BK;
@@ -1910,7 +1959,7 @@ Plan plan_right(const GemmShape& s) {
 // FP8 right sketch: the same tiling as the BF16 right sketch, splits of
 // whole 128-column stages.
 Plan plan_right_q(const GemmShape& s) {
-  Plan pl = plan_right(s);
+  Plan pl = plan_right(s, 2);
   int64_t chunk = (s.L + pl.splits - 1) / pl.splits;
   chunk = (chunk + QK - 1) / QK * QK;
   pl.chunk = chunk;
@@ -1959,6 +2008,24 @@ bool encode_q8_map(CUtensorMap* map, const uint8_t* Aq, int64_t m, int64_t n, in
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int64_t quad_slots() {
+  static int64_t cache = 0;
+  if (cache != 0) return cache;
+  if (set_smem_attr_right() != cudaSuccess) return cache = -1;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config<true>(&cfg, attr, dim3(4, 1, 1), nullptr, 4);
+  cfg.dynamicSmemBytes = CfgR::SMEM;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_sketch_bf16x2_right<kGaussian>, &cfg) !=
+          cudaSuccess ||
+      clusters <= 0) {
+    cudaGetLastError();
+    return cache = -1;
+  }
+  return cache = static_cast<int64_t>(clusters) * 4;
+}
+
 template <int DIST>
 cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 grid,
                          cudaStream_t st) {
@@ -1966,7 +2033,7 @@ cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 gr
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  fill_config<true>(&cfg, attr, grid, st);
+  fill_config<true>(&cfg, attr, grid, st, 4);
   cfg.dynamicSmemBytes = CfgR::SMEM;
   return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_right<DIST>, map, p);
 }

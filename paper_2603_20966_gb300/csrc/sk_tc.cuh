@@ -68,7 +68,8 @@ struct Abort {
 // 4 = worker; barrier 0 = staging full, 1 = staging empty, 2 = operand full,
 // 3 = operand empty, 4 = accumulator full, 5 = accumulator empty, 8 = work
 // queue slot free, 9 = work item published (reported by the reading role's
-// first site code in use, 0x19).
+// first site code in use, 0x19), 6 = rows of the S tile copied in by the
+// partner CTA of the other pair (right sketch).
 
 // Record a give-up: raise the CTA's abort flag and, if this is the launch's
 // first, SK_ETIMEOUT with the site, stage and CTA in the status words.
@@ -251,6 +252,23 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
+// Asynchronous copy of `bytes` (a multiple of 16) from this CTA's shared
+// memory to shared memory of a CTA of the cluster, completing `bytes` of
+// transaction count on the mbarrier at `mbar` in that CTA (both given as
+// shared::cluster addresses).  The source must be visible to the async proxy
+// (fence.proxy.async after the writes that made it).
+__device__ __forceinline__ void bulk_copy_to_cluster(uint32_t dst, uint32_t src, uint32_t bytes,
+                                                     uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];" ::"r"(dst),
+      "r"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+// Named barrier over `threads` threads (a multiple of 32) of this CTA.
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
 // Arrive with release semantics at cluster scope, after this thread's stores
 // into another CTA's shared memory that the waiting side reads.
 __device__ __forceinline__ void mbar_arrive_release_cluster(uint32_t cluster_addr) {
@@ -313,6 +331,15 @@ __device__ __forceinline__ void mma_commit_pair_both(uint32_t bar) {
       "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
       " [%0], %1;" ::"r"(bar),
       "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+// The same, arriving on `bar` in every CTA of the cluster whose bit is set
+// in `mask` (bit i = cluster rank i).
+__device__ __forceinline__ void mma_commit_pair_mask(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
