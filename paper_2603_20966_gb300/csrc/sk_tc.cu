@@ -133,9 +133,10 @@ constexpr uint32_t SBO = 256;  // 8-row groups
 // The S tile of a stage: KSTEPS K-major slabs [128 rows][16] of 4 KB.
 constexpr uint32_t S_SLAB = BM * BK * 2;
 // MN-major 128-byte-swizzled split A tile as the TMA box lays it out:
-// [hi/lo][64-column chunk][32 rows][64 columns]; atoms of 8 rows x 128 B.
+// [hi/lo][64-column chunk][32 rows][64 columns]; atoms of 8 rows x 128 B
+// (next 64 columns: HCHUNK_BYTES, or 2 HCHUNK_BYTES when the tile is split in
+// place as [chunk][hi/lo], see convert_stage).
 constexpr uint32_t HCHUNK_BYTES = LK * HCHUNK * 2;  // 4096: one chunk of one stage
-constexpr uint32_t B_LBO = HCHUNK_BYTES;            // next 64 columns
 constexpr uint32_t B_SBO = 8 * HCHUNK * 2;          // 1024: next 8 rows of m
 constexpr uint32_t B_KSTEP = BK * HCHUNK * 2;       // 2048: next 16 rows of m
 
@@ -151,6 +152,12 @@ struct alignas(128) LeftProblem {
   int dist;         // sk_dist of S
   int chain;        // stages per TMEM accumulation chain (a power of two, multiple of 8)
   PhiloxKey key;
+  // conv_inline: the TMA brings FP32 A ({32 columns, rows, 32-column blocks},
+  // 128-byte swizzle, `amap`) and the workers split it into the BF16 halves in
+  // place (single Rademacher sketches; see convert_stage); 0: the split pass
+  // wrote the halves and `map` loads them
+  int conv_inline;
+  CUtensorMap amap;
 };
 
 // A unit of work: tile (tp, tq) of split z of problem `prob`.  With pairs,
@@ -317,6 +324,52 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
   g.chain = g.pr->chain;
   g.coff = ((it.tp * 7 + it.z * 13 + it.tq * 5) & 7) * (g.chain / 8);
   return g;
+}
+
+// Split this CTA's FP32 A tile of a stage in place into its BF16 halves
+// (hi = bf16(a), lo = bf16(a - hi), as the split pass does).  The TMA leaves
+// the tile as 32-column blocks [block][32 rows][32 floats] with the 128-byte
+// swizzle (16-byte unit u of row r stored at unit u ^ (r mod 8)); 64-column
+// chunk c (blocks 2c and 2c+1, 8 KB) becomes hi chunk c (4 KB) followed by lo
+// chunk c (4 KB), each [32 rows][64 BF16] with the 128-byte swizzle: the
+// MN-major operand layout the MMA reads, chunk after chunk.  Warp w of the
+// worker group converts rows 8w .. 8w+7 (4 lanes per row, 16 columns each):
+// the bytes those rows occupy in blocks 2c and 2c+1 are exactly the bytes
+// they occupy in hi and lo chunk c, so each warp reads its values of a chunk,
+// synchronises itself, and writes them back, with no other warp involved.
+template <class C>
+__device__ __forceinline__ void convert_stage(uint8_t* slot, int cols, int wt) {
+  static_assert(C::GROUP_THREADS == 128, "4 threads per row of a 32-row stage");
+  const uint32_t r = static_cast<uint32_t>(wt) >> 2;  // row of the stage
+  const uint32_t j = static_cast<uint32_t>(wt) & 3u;  // 16-column quarter of the chunk
+  const uint32_t sw = r & 7u;
+  const uint32_t u0 = ((2u * j) ^ sw) * 16u, u1 = ((2u * j + 1u) ^ sw) * 16u;
+  for (int c = 0; c < cols / HCHUNK; ++c) {
+    uint8_t* ch = slot + c * (2 * HCHUNK_BYTES);
+    const uint8_t* src = ch + (j >> 1) * HCHUNK_BYTES + r * 128u;
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t u = (((j & 1u) * 4u + static_cast<uint32_t>(i)) ^ sw) * 16u;
+      const float4 v = *reinterpret_cast<const float4*>(src + u);
+      a[4 * i] = v.x; a[4 * i + 1] = v.y; a[4 * i + 2] = v.z; a[4 * i + 3] = v.w;
+    }
+    __syncwarp();  // this warp's rows of the chunk have been read
+    uint32_t hw[8], lw[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
+      const float2 hv = f2(__uint_as_float(hw[e] << 16), __uint_as_float(hw[e] & 0xffff0000u));
+      // a - hi of both elements in one packed FMA (the product by -1 is exact)
+      const float2 lv = __ffma2_rn(hv, f2(-1.0f, -1.0f), f2(a[2 * e], a[2 * e + 1]));
+      lw[e] = pack_bf16x2(lv.x, lv.y);
+    }
+    uint8_t* hrow = ch + r * 128u;
+    *reinterpret_cast<uint4*>(hrow + u0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(hrow + u1) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+    *reinterpret_cast<uint4*>(hrow + HCHUNK_BYTES + u0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    *reinterpret_cast<uint4*>(hrow + HCHUNK_BYTES + u1) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+  }
 }
 
 // Generate this CTA's BF16 S tile [128 x 32] of one stage (two K-major slabs
@@ -531,6 +584,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             (DIST == kStored ? C::OPS : 0u);               // + the S tile
         const int32_t z0 =
             static_cast<int32_t>((ig.q0 + static_cast<int64_t>(rank) * ig.cols) / HCHUNK);
+        const bool conv = DIST == kRademacher && ig.pr->conv_inline;  // FP32 A, split in place
+        if (conv) tma_prefetch_desc(&ig.pr->amap);
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
           // the MMAs that read this slot last time have completed
@@ -538,7 +593,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (g == sc.stall_stage) continue;  // injected stall: this stage never lands
           mbar_arrive_expect_tx(full_b(so), tx);
           const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * LK);
-          tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
+          if (conv)  // FP32 A: this CTA's columns in 32-column blocks
+            tma_load_3d(sbase + C::OFF_B + so * C::OPB, &ig.pr->amap, 0, y, 2 * z0, full_b(so));
+          else
+            tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
           if (DIST == kStored)  // S rows p0.., columns y.. of the stage, in the operand layout
             tma_load_5d(sbase + C::OFF_S + so * C::OPS, &ig.pr->smap, 0, 0, 0,
                         static_cast<int32_t>(ig.p0 / 8), y / 16, full_b(so));
@@ -560,15 +618,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const uint32_t idesc =
             idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
-        const uint32_t pstride = static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
-        const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * HCHUNK_BYTES;
+        // split A as loaded: [hi chunks][lo chunks] of 64 columns (4 KB each),
+        // or, converted in place, [chunk][hi, lo] (8 KB per chunk)
+        const bool inl = DIST == kRademacher && ig.pr->conv_inline;
+        const uint32_t chunk_stride = inl ? 2 * HCHUNK_BYTES : HCHUNK_BYTES;
+        const uint32_t pstride =
+            inl ? HCHUNK_BYTES : static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
+        const uint32_t hstride = static_cast<uint32_t>(ig.bh / HCHUNK) * chunk_stride;
         // A descriptor holds its operand's address / 16 in its low 14 bits.
         // Every offset below is a multiple of 16 B and every operand lies
         // below 256 KB, so adding offset / 16 to a base descriptor's low word
         // gives exactly the descriptor of the offset operand; the issuer adds
         // instead of rebuilding each descriptor.
         const uint64_t a_base = smem_desc(sbase + C::OFF_S, LBO, SBO);
-        const uint64_t b_base = smem_desc_sw128(sbase + C::OFF_B, B_LBO, B_SBO);
+        const uint64_t b_base = smem_desc_sw128(sbase + C::OFF_B, chunk_stride, B_SBO);
         const uint32_t a_lo = static_cast<uint32_t>(a_base);
         const uint64_t a_hi = a_base & 0xFFFFFFFF00000000ull;
         const uint32_t b_lo = static_cast<uint32_t>(b_base);
@@ -768,6 +831,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!__all_sync(0xffffffffu, ok)) {
           stop = true;
           break;
+        }
+        if constexpr (DIST == kRademacher && PAIR && !NARROW) {
+          // FP32 A: split it here (the sign bits leave the workers idle)
+          if (ig.pr->conv_inline)
+            convert_stage<C>(smem + C::OFF_B + so * C::OPB, ig.cols, wt);
         }
         fence_proxy_async_smem();  // the S tile is read by the tensor core
         __syncwarp();
@@ -1019,19 +1087,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- workers: this CTA's half of the S tile, and its 256 rows of A ----
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
     const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
-    const bool gfirst = wt < 32;  // the group's first warp does its copies and expect-tx
-    // the rows this CTA generates: whole 8-row groups, contiguous in the K-major
-    // layout (256 B per group), copied as one block
-    const uint32_t s_off = static_cast<uint32_t>(gbase / 8) * 256u;
-    const uint32_t s_bytes = static_cast<uint32_t>(gq) * 32u;
-    constexpr int RAD_IT = (2 * 128 + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
-    uint32_t cached_blk[RAD_IT];
-    uint4 words[RAD_IT];
-#pragma unroll
-    for (int it = 0; it < RAD_IT; ++it) {
-      cached_blk[it] = 0xffffffffu;
-      words[it] = make_uint4(0u, 0u, 0u, 0u);
-    }
+    static_assert(C::GROUP_WARPS == 4, "16 generated rows per warp cover gq <= 64");
+    const int wg = wt >> 5;       // warp of the group
+    const bool gfirst = wg == 0;  // registers the expected bytes and waits for them
+    // warp wg generates rows 16 wg .. 16 wg + 15 of this CTA's generated rows
+    // (whole 8-row groups: 256 contiguous bytes each in the K-major layout)
+    // and copies them into the partner itself, so no barrier spans the group
+    const int wrows = max(0, min(16, gq - 16 * wg));
+    const uint32_t w_off = static_cast<uint32_t>(gbase + 16 * wg) * 32u;
+    const uint32_t w_bytes = static_cast<uint32_t>(wrows) * 32u;
+    const uint32_t s_bytes = static_cast<uint32_t>(gq) * 32u;  // from all four partner warps
+    uint32_t cached_blk = 0xffffffffu;
+    uint4 words = make_uint4(0u, 0u, 0u, 0u);
+    int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
     for (int s = grp; s < nsteps; s += C::NGROUPS) {
       const int sf = s % C::NSF;
       const int so = s % C::NSO;
@@ -1041,27 +1109,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
       // the partner's half of this CTA's S rows will land here
-      if (gfirst && lane == 0) mbar_arrive_expect_tx(s_recv(so), s_bytes);
+      if (gfirst) {
+        if (lane == 0) mbar_arrive_expect_tx(s_recv(so), s_bytes);
+        pend = s;
+      }
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
       if (DIST == kRademacher) {
-#pragma unroll
-        for (int it = 0; it < RAD_IT; ++it) {
-          const int t = wt + it * C::GROUP_THREADS;
-          if (t >= 2 * gq) break;
-          const uint32_t r = static_cast<uint32_t>(gbase + t % gq);
-          const uint32_t hh = static_cast<uint32_t>(t / gq);
+        // a lane: one row (16 wg + lane % 16) and one 8-column half (lane / 16)
+        if ((lane & 15) < wrows) {
+          const uint32_t r = static_cast<uint32_t>(gbase + 16 * wg + (lane & 15));
+          const uint32_t hh = static_cast<uint32_t>(lane >> 4);
           const int64_t grow = g0 + r;
           const int64_t c0 = cbase + 8 * hh;
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           if (grow < p.Q && c0 < lend) {
             const uint32_t c = static_cast<uint32_t>(c0);
             const uint32_t blk = c >> 7;
-            if (blk != cached_blk[it]) {
-              words[it] = rademacher_bits(p.rk, static_cast<uint32_t>(grow), blk, 0u);
-              cached_blk[it] = blk;
+            if (blk != cached_blk) {
+              words = rademacher_bits(p.rk, static_cast<uint32_t>(grow), blk, 0u);
+              cached_blk = blk;
             }
             const uint32_t wsel = (c >> 5) & 3u;
-            const uint4 wv = words[it];
+            const uint4 wv = words;
             const uint32_t w = wsel == 0 ? wv.x : wsel == 1 ? wv.y : wsel == 2 ? wv.z : wv.w;
             const uint32_t bits = w >> (c & 31u);
             v.x = 0x3F803F80u | ((bits & 1u) << 15) | ((bits & 2u) << 30);
@@ -1072,19 +1141,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
         }
       } else {
-        // thread wt owns quad qd of rows gbase + rb + RSTEP it (4 quads per row)
-        constexpr int RSTEP = C::GROUP_THREADS / 4;
-        constexpr int GEN_IT = 64 / RSTEP;  // rows of the generated half: gq <= 64
-        static_assert(RSTEP % 8 == 0 && GEN_IT >= 1, "row passes of the worker group");
-        const uint32_t qd = static_cast<uint32_t>(wt) & 3u;
-        const uint32_t rb = static_cast<uint32_t>(wt) >> 2;
+        // a lane owns quad qd of rows 16 wg + 8 it + lane / 4 (4 quads per row)
+        const uint32_t qd = static_cast<uint32_t>(lane) & 3u;
         const bool cv = cbase + 4 * qd < lend;
         const uint32_t j = static_cast<uint32_t>(cbase >> 2) + qd;  // Philox block
-#pragma unroll 2
-        for (int it = 0; it < GEN_IT; ++it) {
-          const uint32_t rr = rb + static_cast<uint32_t>(RSTEP * it);
-          if (rr >= static_cast<uint32_t>(gq)) break;
-          const uint32_t r = static_cast<uint32_t>(gbase) + rr;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+          const int rr = 8 * it + (lane >> 2);
+          if (rr >= wrows) break;
+          const uint32_t r = static_cast<uint32_t>(gbase + 16 * wg + rr);
           const int64_t grow = g0 + r;
           uint2 v = make_uint2(0u, 0u);
           if (grow < p.Q && cv) {
@@ -1097,13 +1162,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint2*>(sdst + off) = v;
         }
       }
-      // the group's rows are written: copy them into the partner (async
+      // this warp's rows are written: copy them into the partner (async
       // proxy, completing on its s_recv barrier)
       fence_proxy_async_smem();
-      named_bar_sync(1u + static_cast<uint32_t>(grp), C::GROUP_THREADS);
-      if (gfirst && lane == 0)
-        bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + s_off,
-                             smem_u32(sdst) + s_off, s_bytes, partner_s_recv + 8u * so);
+      __syncwarp();
+      if (lane == 0 && w_bytes != 0)
+        bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + w_off,
+                             smem_u32(sdst) + w_off, w_bytes, partner_s_recv + 8u * so);
       ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
@@ -1138,12 +1203,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       fence_proxy_async_smem();
       ok = !gfirst || mbar_wait(s_recv(so), (s / C::NSO) & 1, ab, 0x46, s);
       if (!__all_sync(0xffffffffu, ok)) break;
+      pend = -1;
       __syncwarp();
       if (lane == 0) {
         mbar_arrive_cluster(lead_full_o + 8u * so);
         mbar_arrive(empty_f(sf));
       }
     }
+    // leaving early: let a copy the partner may still be sending land first
+    if (gfirst && pend >= 0 && lane == 0)
+      drain_wait(s_recv(pend % C::NSO), (pend / C::NSO) & 1, 100000000ull);
   }
 
   tc_fence_before();
@@ -1872,10 +1941,35 @@ bool encode_stored_map(CUtensorMap* map, const void* S, int64_t k, int64_t m, in
 // Rademacher sketches drain the accumulator half as often as the others.
 int left_chain_stages(int dist) { return dist == kRademacher ? 2 * CHAIN_L : CHAIN_L; }
 
+// FP32 A[m x n] (row stride lda, n a multiple of 32) as a 3D tensor {32
+// columns, m rows, n / 32 blocks of 32 columns}: one box = `cols` columns of
+// 32 rows, as blocks [block][32 rows][32 floats] with the 128-byte swizzle.
+bool encode_fp32_blocks_map(CUtensorMap* map, const float* A, int64_t m, int64_t n, int64_t lda,
+                            int cols) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t gdim[3] = {32, static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n / 32)};
+  const cuuint64_t gstride[2] = {static_cast<cuuint64_t>(lda) * 4, 128};
+  const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(LK), static_cast<cuuint32_t>(cols / 32)};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(A), gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A_inline: FP32 A (row stride lda) that the kernel splits in place instead
+// of reading the split pass's halves from H (Rademacher pair sketches with n
+// a multiple of 32), or null.
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
-                  float* part, uint64_t seed, int dist) {
+                  float* part, uint64_t seed, int dist, const float* A_inline = nullptr,
+                  int64_t lda = 0) {
   memset(pr, 0, sizeof(*pr));
   if (!encode_split_map(&pr->map, H, s.L, s.Q, pl.pair ? pl.nt / 2 : pl.nt)) return false;
+  if (A_inline != nullptr) {
+    if (!encode_fp32_blocks_map(&pr->amap, A_inline, s.L, s.Q, lda, pl.pair ? pl.nt / 2 : pl.nt))
+      return false;
+    pr->conv_inline = 1;
+  }
   pr->part = part;
   pr->P = s.P;
   pr->Q = s.Q;
@@ -2241,7 +2335,10 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
   const int64_t units = pl.pair ? pair_slots() / 2 : num_sms_tc();
   HostSched hs;
   hs.probs.resize(1);
-  if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist))
+  // Rademacher pair sketches split A inside the kernel (their workers are
+  // otherwise idle); the others read the halves the split pass writes
+  const bool conv = S_stored == nullptr && h->dist == kRademacher && pl.pair && s.Q % 32 == 0;
+  if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist, conv ? A : nullptr, lda))
     return cudaErrorInvalidValue;
   if (S_stored && !encode_stored_map(&hs.probs[0].smap, S_stored, s.P, s.L, lds))
     return cudaErrorInvalidValue;
@@ -2257,9 +2354,10 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
   const LeftSched sc = device_sched(hs, hm->d_sched, h->d_status, h->wait_limit_ns,
                                     h->stall_stage);
   const int64_t nunits = hs.units;
-  // the measurement hook brackets both passes: split of A, then the sketch
+  // the measurement hook brackets both passes: split of A (unless the kernel
+  // splits it), then the sketch
   prof_mark(h->prof_start, st);
-  cudaError_t e = split_launch_one(A, lda, s.L, s.Q, H, st);
+  cudaError_t e = conv ? cudaSuccess : split_launch_one(A, lda, s.L, s.Q, H, st);
   if (e != cudaSuccess) return e;
   const int mode = S_stored ? kStored : h->dist;
   e = pl.pair ? launch_left_dist<true>(mode, sc, nunits, st)

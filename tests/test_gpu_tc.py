@@ -46,7 +46,10 @@ def run_left(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
 
 
 SHAPES = [(128, 4096, 512), (64, 4096, 256), (100, 1000, 48), (130, 777, 300), (1, 16, 16),
-          (3, 5, 7), (256, 70000, 1000), (2048, 65536, 512), (200, 300000, 20)]
+          (3, 5, 7), (256, 70000, 1000), (2048, 65536, 512), (200, 300000, 20),
+          # CTA pairs with n a multiple of 32 (the Rademacher kernel splits A in
+          # place): ragged m, a partly filled second column tile, 96 columns
+          (384, 10007, 544), (256, 3000, 96)]
 
 
 @pytest.mark.parametrize("dist", [R, G])
@@ -72,6 +75,13 @@ def test_identity_gives_scaled_bf16_matrix_exactly(P, orc, dist):
     got = run_left(P, 13, dist, k, torch.eye(m))
     ref = orc.generate(13, dist, BF16, 0, 0, k, m) * orc.scale(k)  # fl32(s * bf16(g))
     np.testing.assert_array_equal(got, ref.astype(np.float32))
+
+
+def test_rademacher_in_place_split_with_padded_rows(P, orc):
+    # lda > n: the FP32 tile the kernel splits in place is read with the row pitch
+    A = _A(5003, 160, 9)
+    got = run_left(P, 21, R, 300, A, lda=176, ldy=164)
+    assert rel_frob(got, orc.apply_left(21, R, BF16, 300, A.numpy())) <= TOL
 
 
 def test_rademacher_bf16x2_agrees_with_fp32_form(P):
