@@ -802,8 +802,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         cached_blk[it] = 0xffffffffu;
         words[it] = make_uint4(0u, 0u, 0u, 0u);
       }
-      for (int s = 0; s < ig.nsteps; ++s, ++g) {
-        if (g % C::NGROUPS != grp) continue;
+      // this group's stages of the item: g_item + s = grp (mod NGROUPS)
+      const int g_item = g;
+      for (int s = ((grp - g_item) % C::NGROUPS + C::NGROUPS) % C::NGROUPS; s < ig.nsteps;
+           s += C::NGROUPS) {
+        g = g_item + s;
         const int so = g % C::NSO;
         // the MMAs that read S tile `so` last time have completed
         bool ok = g < C::NSO || mbar_wait(empty_o(so), ((g / C::NSO) & 1) ^ 1, ab, 0x43, g);
@@ -846,6 +849,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive(full_o(so));
         }
       }
+      g = g_item + ig.nsteps;
     }
   }
 

@@ -117,27 +117,53 @@ def test_leading_dimensions_and_alignment(P, orc):
         P.sk_destroy(h)
 
 
-@pytest.mark.parametrize("dist", [R, G])
-def test_full_size_tall_skinny_sampled(P, orc, dist):
-    # the 2^20 x 512, k = 2048 workload exactly as bench.py launches it
-    m, n, k = 1 << 20, 512, 2048
-    A = _A(m, n, 1, device="cuda")
-    Y = torch.empty((k, n), device="cuda")
+def _full_size_left(P, dist, m, n, k, seed, lda):
+    A = torch.zeros((m, lda), device="cuda")
+    A[:, :n] = _A(m, n, seed, device="cuda")
+    Y = torch.empty((k, lda), device="cuda")
     h = P.sk_create(7, dist, k)
     try:
         P.sk_set_precision(h, BF16)
-        P.sk_apply_left(h, A, m, n, n, Y, n)
+        P.sk_apply_left(h, A, m, n, lda, Y, lda)
         assert P.sk_stream_status(h) == 0
     finally:
         P.sk_destroy(h)
+    return A, Y
+
+
+def _check_row_blocks(orc, dist, k, A, Y, cols, blocks):
+    idx = torch.from_numpy(cols).cuda()
+    a_cols = A[:, idx].cpu().numpy()
+    for rows in blocks:
+        ref = orc.apply_left(7, dist, BF16, k, a_cols, rows=rows)
+        got = Y[rows[0]:rows[0] + rows[1]][:, idx].cpu().numpy()
+        err = rel_frob(got, ref)
+        assert err <= TOL, (rows, err)
+
+
+@pytest.mark.parametrize("dist", [R, G])
+def test_full_size_tall_skinny_sampled(P, orc, dist):
+    # the 2^20 x 512, k = 2048 workload exactly as bench.py launches it; rows
+    # in the first, an inner and the last 256-row tile of k (each tile shifts
+    # its accumulation-chain boundaries differently), columns in both
+    # 256-column halves
+    m, n, k = 1 << 20, 512, 2048
+    A, Y = _full_size_left(P, dist, m, n, k, 1, n)
     cols = np.array([0, 1, 255, 256, 511])
-    a_cols = A[:, torch.from_numpy(cols).cuda()].cpu().numpy()
-    rows = (1000, 96)
-    ref = orc.apply_left(7, dist, BF16, k, a_cols, rows=rows)
-    got = Y[rows[0]:rows[0] + rows[1]][:, torch.from_numpy(cols).cuda()].cpu().numpy()
-    err = rel_frob(got, ref)
-    assert err <= TOL, err
-    assert torch.isfinite(Y).all()
+    _check_row_blocks(orc, dist, k, A, Y, cols, [(0, 32), (1000, 96), (k - 48, 48)])
+    assert torch.isfinite(Y[:, :n]).all()
+
+
+@pytest.mark.parametrize("dist", [R, G])
+def test_full_size_ragged_sampled(P, orc, dist):
+    # near-full size with a ragged tail everywhere: m not a multiple of a
+    # stage or a split of m, n = 500 (second column tile partly filled, no
+    # in-place split), k = 2000 (last 256-row tile of k partly filled)
+    m, n, k = (1 << 20) - 37, 500, 2000
+    A, Y = _full_size_left(P, dist, m, n, k, 2, 500)
+    cols = np.array([0, 255, 256, 480, 499])
+    _check_row_blocks(orc, dist, k, A, Y, cols, [(0, 16), (1790, 16), (k - 32, 32)])
+    assert torch.isfinite(Y[:, :n]).all()
 
 
 def run_right(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
