@@ -337,11 +337,15 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
 // the bytes those rows occupy in blocks 2c and 2c+1 are exactly the bytes
 // they occupy in hi and lo chunk c, so each warp reads its values of a chunk,
 // synchronises itself, and writes them back, with no other warp involved.
+// Lane l takes row 8w + (l mod 8) and column quarter l / 8: the 8 lanes of
+// each 128-byte phase of a 16-byte access then read (and write) one unit of
+// each of 8 rows, and the swizzle puts those 8 units in 8 different bank
+// groups, so no access of the conversion has a bank conflict.
 template <class C>
 __device__ __forceinline__ void convert_stage(uint8_t* slot, int cols, int wt) {
   static_assert(C::GROUP_THREADS == 128, "4 threads per row of a 32-row stage");
-  const uint32_t r = static_cast<uint32_t>(wt) >> 2;  // row of the stage
-  const uint32_t j = static_cast<uint32_t>(wt) & 3u;  // 16-column quarter of the chunk
+  const uint32_t r = (static_cast<uint32_t>(wt) >> 5) * 8u + (static_cast<uint32_t>(wt) & 7u);
+  const uint32_t j = (static_cast<uint32_t>(wt) >> 3) & 3u;  // 16-column quarter of the chunk
   const uint32_t sw = r & 7u;
   const uint32_t u0 = ((2u * j) ^ sw) * 16u, u1 = ((2u * j + 1u) ^ sw) * 16u;
   for (int c = 0; c < cols / HCHUNK; ++c) {
