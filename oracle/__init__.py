@@ -64,8 +64,10 @@ def lib():
             L.orc_philox4x32_10.restype = None
             L.orc_ln.argtypes = [vp, vp, i64]
             L.orc_ln.restype = None
-            L.orc_sincospi.argtypes = [vp, vp, vp, i64]
-            L.orc_sincospi.restype = None
+            L.orc_sincospi_quarter.argtypes = [vp, vp, vp, i64]
+            L.orc_sincospi_quarter.restype = None
+            L.orc_circle.argtypes = [vp, vp, vp, i64]
+            L.orc_circle.restype = None
             L.orc_box_muller.argtypes = [vp, vp, i64]
             L.orc_box_muller.restype = None
             L.orc_bf16_rne.argtypes = [vp, vp, i64]
@@ -113,17 +115,29 @@ def ln(x: np.ndarray) -> np.ndarray:
     return y
 
 
-def sincospi(t: np.ndarray):
-    t = np.ascontiguousarray(t, dtype=np.float32)
-    s = np.empty_like(t)
-    c = np.empty_like(t)
-    lib().orc_sincospi(_p(t), _p(s), _p(c), t.size)
+def sincospi_quarter(r: np.ndarray):
+    """(sin(pi r), cos(pi r)) for r in [-1/4, 1/4], the generator's FP32 polynomials."""
+    r = np.ascontiguousarray(r, dtype=np.float32)
+    s = np.empty_like(r)
+    c = np.empty_like(r)
+    lib().orc_sincospi_quarter(_p(r), _p(s), _p(c), r.size)
     return s, c
+
+
+def circle(words: np.ndarray):
+    """The circle point (X, Y) of each angle word (uint32): the position of
+    bits 29..8 turned by the quarter turns of bits 31..30."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    x = np.empty(w.shape, dtype=np.float32)
+    y = np.empty(w.shape, dtype=np.float32)
+    lib().orc_circle(_p(w), _p(x), _p(y), w.size)
+    return x, y
 
 
 def box_muller(words: np.ndarray) -> np.ndarray:
     """Box-Muller of each word pair (row of ``words``, shape [N, 2], uint32):
-    the generator's Gaussian pair (rho cospi(2 u2), rho sinpi(2 u2)), shape [N, 2]."""
+    the generator's Gaussian pair (rho X, rho Y) with (X, Y) the circle
+    point of the second word, shape [N, 2]."""
     w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1, 2)
     z = np.empty(w.shape, dtype=np.float32)
     lib().orc_box_muller(_p(w), _p(z), w.shape[0])

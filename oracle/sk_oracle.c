@@ -6,7 +6,8 @@
  * and by the cpu_baseline / reference leg of bench.py.  It shares no code,
  * header, table or constant generator with the CUDA path: every constant here
  * is written out from its mathematical definition (Philox from Salmon et al.
- * 2011; polynomial coefficients from the Taylor series of atanh, sin and cos).
+ * 2011; polynomial coefficients from the Taylor series of sin and cos and,
+ * for ln, from the least-squares fit that oracle/fit_ln.py writes out).
  *
  * What it computes (arXiv 2603.20966, Sec. 1 and Sec. 3 "Lower Bounds and
  * Algorithm for Matrix Multiplication with a Random Matrix"):
@@ -34,15 +35,19 @@
  *   dom     = 0 for the sketching matrix.
  *   Gaussian (Box-Muller): entries c = 4j..4j+3 use the words (x0,x1) for
  *     c mod 4 in {0,1} and (x2,x3) for c mod 4 in {2,3};
- *     u1 = ((xa >> 8) + 1) * 2^-24 in (0,1],  u2 = (xb >> 8) * 2^-24 in [0,1)
- *     rho = sqrt(-2 ln u1),  t = 2 u2,
- *     g = rho * cospi(t) for even c, rho * sinpi(t) for odd c.
+ *     u1 = ((xa >> 8) + 1) * 2^-24 in (0,1],  rho = sqrt(-2 ln u1);
+ *     the angle from the top 24 bits of xb: w = bits 29..8, the position
+ *     r = w 2^-23 - 1/4 in [-1/4, 1/4), (C, S) = (cospi r, sinpi r), and
+ *     (X, Y) = (C, S) turned by q = bits 31..30 quarter turns:
+ *     (C, S), (-S, C), (-C, -S), (S, -C) -- the angle pi r + q pi/2, so the
+ *     2^24 words give the 2^24 multiples of 2 pi / 2^24, each once;
+ *     g = rho * X for even c, rho * Y for odd c.
  *   Rademacher: bit (c mod 32) of word ((c >> 5) mod 4); set bit -> -1.
  *   Uniform: u = (x_{c mod 4} >> 8) * 2^-24 in [0,1) (the distribution the
  *     paper's experiments draw, Sec. 6.2).
- *   ln and sincospi are this library's own FP32 routines built only from
- *   round-to-nearest add, mul, fma, div and sqrt, so that CPU and GPU agree
- *   bit for bit.
+ *   ln, sinpi and cospi are this library's own FP32 polynomials built only
+ *   from round-to-nearest add, mul and fma (and sqrt for rho), so that CPU
+ *   and GPU agree bit for bit.
  */
 #include <math.h>
 #include <pthread.h>
@@ -99,16 +104,16 @@ static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 
 /* ------------------------------------------------------------------------ */
 /* Natural logarithm on (0, 1], FP32.                                         */
-/* x = 2^e f with f folded into [sqrt(1/2), sqrt(2)]; with s = (f-1)/(f+1),  */
-/* ln f = 2 atanh s = 2s + s^3 (2/3 + s^2 (2/5 + s^2 (2/7 + s^2 2/9)));      */
-/* ln x = e*LN2_HI + (e*LN2_LO + ln f), LN2_HI holding the leading 16 bits   */
-/* of ln 2 so that e*LN2_HI is exact (Cody-Waite).                           */
+/* x = 2^e f with f folded into [sqrt(1/2), sqrt(2)) (f > fl32(sqrt 2) is     */
+/* halved and e raised by one); t = f - 1 (exact); ln f = t + t^2 Q(t) with  */
+/* Q the degree-8 least-squares fit of (ln(1+t) - t) / t^2 written out by    */
+/* oracle/fit_ln.py; ln x = e*LN2_HI + (e*LN2_LO + ln f), LN2_HI holding the  */
+/* leading 16 bits of ln 2 so that e*LN2_HI is exact (Cody-Waite).           */
 /* ------------------------------------------------------------------------ */
 float orc_ln1(float x) {
-  const float two_3 = 0x1.555556p-1f;   /* 2/3 rounded to FP32 */
-  const float two_5 = 0x1.99999ap-2f;   /* 2/5 */
-  const float two_7 = 0x1.24924ap-2f;   /* 2/7 */
-  const float two_9 = 0x1.c71c72p-3f;   /* 2/9 */
+  static const float q[9] = {
+      -0x1.fffff8p-2f, 0x1.555558p-2f, -0x1.000422p-2f, 0x1.999fc2p-3f, -0x1.5424e0p-3f,
+      0x1.22bf86p-3f, -0x1.0f9b0cp-3f, 0x1.068b28p-3f, -0x1.321a48p-4f};
   const float ln2_hi = 0x1.62e4p-1f;    /* 0.693145751953125 */
   const float ln2_lo = 0x1.7f7d1cp-20f; /* ln 2 - ln2_hi rounded to FP32 */
   uint32_t b = f2u(x);
@@ -120,25 +125,20 @@ float orc_ln1(float x) {
   } else {
     mb |= 0x3f800000u;
   }
-  float f = u2f(mb);
-  float s = (f - 1.0f) / (f + 1.0f);
-  float s2 = s * s;
-  float p = fmaf(s2, two_9, two_7);
-  p = fmaf(s2, p, two_5);
-  p = fmaf(s2, p, two_3);
-  float s3 = s * s2;
-  float lnf = fmaf(s3, p, s + s);
+  float t = u2f(mb) - 1.0f;
+  float p = q[8];
+  for (int i = 7; i >= 0; --i) p = fmaf(t, p, q[i]);
+  float lnf = fmaf(t * t, p, t);
   float ef = (float)e;
   return fmaf(ef, ln2_hi, fmaf(ef, ln2_lo, lnf));
 }
 
 /* ------------------------------------------------------------------------ */
-/* sin(pi t), cos(pi t) for t in [0, 2), FP32.                                */
-/* q = rint(2t) (ties to even), r = t - q/2 in [-1/4, 1/4] (exact), then the */
-/* Taylor series of sin(pi r) to r^9 and cos(pi r) to r^10, coefficients     */
-/* (-1)^j pi^n / n! rounded once to FP32, rotated by q quarter turns.        */
+/* sin(pi r), cos(pi r) for r in [-1/4, 1/4], FP32: the Taylor series of     */
+/* sin(pi r) to r^9 and cos(pi r) to r^10, coefficients (-1)^j pi^n / n!     */
+/* rounded once to FP32.                                                     */
 /* ------------------------------------------------------------------------ */
-void orc_sincospi1(float t, float* sin_out, float* cos_out) {
+void orc_sincospi_quarter1(float r, float* sin_out, float* cos_out) {
   const float s1 = 0x1.921fb6p+1f;   /*  pi        */
   const float s3 = -0x1.4abbcep+2f;  /* -pi^3/3!   */
   const float s5 = 0x1.466bc6p+1f;   /*  pi^5/5!   */
@@ -149,33 +149,50 @@ void orc_sincospi1(float t, float* sin_out, float* cos_out) {
   const float c6 = -0x1.55d3c8p+0f;  /* -pi^6/6!   */
   const float c8 = 0x1.e1f506p-3f;   /*  pi^8/8!   */
   const float c10 = -0x1.a6d1f2p-6f; /* -pi^10/10! */
-  float qf = rintf(t + t);          /* default rounding mode: nearest-even */
-  int q = (int)qf;
-  float r = t - qf * 0.5f;
   float r2 = r * r;
   float sp = fmaf(r2, s9, s7);
   sp = fmaf(r2, sp, s5);
   sp = fmaf(r2, sp, s3);
   sp = fmaf(r2, sp, s1);
-  float sn = r * sp;
+  *sin_out = r * sp;
   float cp = fmaf(r2, c10, c8);
   cp = fmaf(r2, cp, c6);
   cp = fmaf(r2, cp, c4);
   cp = fmaf(r2, cp, c2);
-  float cs = fmaf(r2, cp, 1.0f);
-  switch (q & 3) {
-    case 0: *sin_out = sn; *cos_out = cs; break;
-    case 1: *sin_out = cs; *cos_out = -sn; break;
-    case 2: *sin_out = -sn; *cos_out = -cs; break;
-    default: *sin_out = -cs; *cos_out = sn; break;
+  *cos_out = fmaf(r2, cp, 1.0f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The point (X, Y) on the unit circle of an angle word w (its top 24 bits): */
+/* position r = w' 2^-23 - 1/4 with w' = bits 29..8 (0.5 + w' 2^-23 and its  */
+/* difference with 3/4 are exact), (C, S) = (cospi r, sinpi r), turned by a  */
+/* quarter turn when bit 30 is set and by a half turn when bit 31 is set.    */
+/* ------------------------------------------------------------------------ */
+void orc_circle1(uint32_t w, float* x, float* y) {
+  float r = u2f(0x3f000000u | ((w >> 7) & 0x007ffffeu)) - 0.75f;
+  float sn, cs;
+  orc_sincospi_quarter1(r, &sn, &cs);
+  float px = cs, py = sn;
+  if (w & 0x40000000u) { /* (x, y) -> (-y, x) */
+    px = -sn;
+    py = cs;
   }
+  if (w & 0x80000000u) { /* (x, y) -> (-x, -y) */
+    px = -px;
+    py = -py;
+  }
+  *x = px;
+  *y = py;
 }
 
 void orc_ln(const float* x, float* y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = orc_ln1(x[i]);
 }
-void orc_sincospi(const float* t, float* s, float* c, int64_t n) {
-  for (int64_t i = 0; i < n; ++i) orc_sincospi1(t[i], s + i, c + i);
+void orc_sincospi_quarter(const float* r, float* s, float* c, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) orc_sincospi_quarter1(r[i], s + i, c + i);
+}
+void orc_circle(const uint32_t* w, float* x, float* y, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) orc_circle1(w[i], x + i, y + i);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -263,16 +280,15 @@ static double quantize(float g, int prec) {
 }
 
 /* Box-Muller on one pair of Philox words (xa, xb):                         */
-/* u1 = ((xa >> 8) + 1) 2^-24 in (0, 1], u2 = (xb >> 8) 2^-24 in [0, 1),     */
-/* rho = sqrt(-2 ln u1), z[0] = rho cospi(2 u2), z[1] = rho sinpi(2 u2).     */
+/* u1 = ((xa >> 8) + 1) 2^-24 in (0, 1], rho = sqrt(-2 ln u1), (X, Y) the    */
+/* circle point of xb, z[0] = rho X, z[1] = rho Y.                           */
 static void box_muller(uint32_t xa, uint32_t xb, float z[2]) {
   float u1 = (float)((xa >> 8) + 1u) * 0x1p-24f;
-  float u2 = (float)(xb >> 8) * 0x1p-24f;
   float rho = sqrtf(-2.0f * orc_ln1(u1));
-  float sn, cs;
-  orc_sincospi1(u2 + u2, &sn, &cs);
-  z[0] = rho * cs;
-  z[1] = rho * sn;
+  float x, y;
+  orc_circle1(xb, &x, &y);
+  z[0] = rho * x;
+  z[1] = rho * y;
 }
 
 /* z[2i], z[2i+1] = Box-Muller of the word pair (w[2i], w[2i+1]), i < npairs. */

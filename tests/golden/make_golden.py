@@ -3,7 +3,7 @@
 The file freezes a few generated entries g(r, c) (FP32 bit patterns) and the
 Philox words behind them, so that any later change to the generator
 specification (key/counter layout, Box-Muller mapping, Rademacher bit order,
-the own ln/sincospi) is visible as a diff.  Values come only from oracle/;
+the own ln and circle map) is visible as a diff.  Values come only from oracle/;
 the Philox words are the ones pinned to cuRAND's host generator by
 tests/test_oracle_philox.py.
 

@@ -22,17 +22,17 @@ def test_box_muller_radius_and_angle(orc, seed, row):
     g = orc.generate(seed, G, 0, row, 0, 1, ncols)[0].astype(np.float64)
     x = _words(orc, seed, row, np.arange(ncols // 4))
     for pair in (0, 1):
-        xa, xb = x[:, 2 * pair].astype(np.float64), x[:, 2 * pair + 1].astype(np.float64)
+        xa = x[:, 2 * pair].astype(np.float64)
         u1 = (np.floor(xa / 256) + 1) / 2.0**24
-        u2 = np.floor(xb / 256) / 2.0**24
         z0 = g[2 * pair::4]
         z1 = g[2 * pair + 1::4]
         r2 = z0 * z0 + z1 * z1
         np.testing.assert_allclose(r2, -2.0 * np.log(u1), rtol=2e-6, atol=1e-6)
+        # the angle is the circle point's (pinned on its own) of the pair's
+        # second word
+        cx, cy = orc.circle(x[:, 2 * pair + 1])
         big = r2 > 1e-6
-        ang = np.mod(np.arctan2(z1[big], z0[big]) / (2 * np.pi), 1.0)
-        d = np.abs(ang - u2[big])
-        d = np.minimum(d, 1 - d)
+        d = np.abs(np.angle((z0[big] + 1j * z1[big]) / (cx[big] + 1j * cy[big].astype(np.float64))))
         assert d.max() < 1e-5
 
 
@@ -124,24 +124,24 @@ def test_scale(orc):
 
 
 def test_box_muller_every_input_against_fp64(orc):
-    """orc_box_muller over every u1 (with u2 running through every value in
-    the same order) and, in a second pass, every u2 against a fixed mid-range
-    u1: the radius matches sqrt(-2 ln u1) and the angle 2 pi u2 in FP64."""
+    """orc_box_muller over every u1 (with the angle word running through
+    every value of its top 24 bits in the same order): the radius matches
+    sqrt(-2 ln u1) in FP64 and the angle is the multiple of 2 pi / 2^24 that
+    the circle map assigns to the word."""
     n = 1 << 24
     i = np.arange(n, dtype=np.uint64)
     words = np.stack([((i << 8) | 0x11).astype(np.uint32),
                       (((n - 1 - i) << 8) | 0xEE).astype(np.uint32)], 1)
     z = orc.box_muller(words).astype(np.float64)
     u1 = (i.astype(np.float64) + 1) / 2.0**24
-    u2 = (n - 1 - i).astype(np.float64) / 2.0**24
     r = np.sqrt(z[:, 0] ** 2 + z[:, 1] ** 2)
     rho = np.sqrt(-2.0 * np.log(u1))
     assert np.all(np.abs(r - rho) <= 4e-7 * np.maximum(rho, 1.0))
     assert r[-1] == 0.0  # u1 = 1: ln 1 = 0 exactly
     big = rho > 1e-2
-    ang = np.mod(np.arctan2(z[big, 1], z[big, 0]) / (2 * np.pi), 1.0)
-    d = np.abs(ang - u2[big])
-    assert np.minimum(d, 1 - d).max() < 2e-6
+    cx, cy = orc.circle(words[:, 1])
+    d = np.abs(np.angle((z[big, 0] + 1j * z[big, 1]) / (cx[big] + 1j * cy[big].astype(np.float64))))
+    assert d.max() < 2e-6
     # the generator's Gaussian entries are these pairs of its Philox words
     x = _words(orc, 7, 3, np.arange(64))
     g = orc.generate(7, G, 0, 3, 0, 1, 256)[0]
