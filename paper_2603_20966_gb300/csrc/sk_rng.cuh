@@ -15,17 +15,18 @@
 //   Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers
 //   0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
 //   Gaussian: Box-Muller on (x0,x1) for c%4 in {0,1}, (x2,x3) for {2,3}:
-//     u1 = ((xa>>8)+1) 2^-24, u2 = (xb>>8) 2^-24, rho = sqrt(-2 ln u1),
-//     g = rho cospi(2 u2) (c even) or rho sinpi(2 u2) (c odd).
+//     u1 = ((xa>>8)+1) 2^-24, rho = sqrt(-2 ln u1); from xb the position
+//     r = (bits 29..8) 2^-23 - 1/4 and (X, Y) = (cospi r, sinpi r) turned by
+//     q = bits 31..30 quarter turns (angle pi r + q pi/2: the 2^24 words give
+//     every multiple of 2 pi / 2^24 once); g = rho X (c even) or rho Y (c odd).
 //   Rademacher: bit c%32 of word (c>>5)%4, set -> -1.
 //   Uniform: (x_{c%4} >> 8) 2^-24.
 // Every floating-point step is an explicitly rounded IEEE operation
 // (__fadd2_rn, __fmul2_rn, __ffma2_rn and their scalar forms), so no
 // compiler contraction or fast-math flag can change a bit.  ln, sin and cos
-// are polynomials; the quotient and the square root of Box-Muller are the
-// correctly rounded IEEE results, computed by Markstein's method from the
-// hardware reciprocal and reciprocal-square-root approximations (see
-// div_x2 / sqrt_x2).
+// are polynomials; the square root of Box-Muller is the correctly rounded
+// IEEE result, computed by Markstein's method from the hardware
+// reciprocal-square-root approximation (see sqrt_x2).
 #pragma once
 #include <stdint.h>
 #include <cuda_bf16.h>
@@ -93,47 +94,18 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 // round each component exactly like the scalar __fadd_rn / __fmul_rn /
 // __fmaf_rn, so every value is the one the specification's scalar steps give
 // while the floating-point work takes half the instructions (the generator
-// is instruction-issue bound inside the sketch kernels).  Division and
-// square root give the IEEE correctly rounded results (div_x2, sqrt_x2).
+// is instruction-issue bound inside the sketch kernels).  The square root
+// gives the IEEE correctly rounded result (sqrt_x2).
 // Where a step below is written differently from the specification, the
 // comment beside it shows that the value is the same.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float2 neg2(float2 x) { return f2(-x.x, -x.y); }
-
-// a / b rounded to nearest-even, for the operands of ln01_x2: b = fl(f + 1)
-// in [1.7, 2.5), a = f - 1.  Markstein's method (P. Markstein, IBM J. Res.
-// Dev. 34(1), 1990): one Newton step on an approximate reciprocal y of b,
-// the quotient q = a y, its exact remainder r = a - b q (one FMA), and the
-// corrected quotient q + r y, rounded once.  The correction rounds correctly
-// except for a divisor with an all-ones significand; the only one in range
-// is 2 - 2^-23, which only f = 1 - 2^-23 produces, so its quotient is the
-// constant -2^-23 / (2 - 2^-23) rounded.  An exhaustive host check runs the
-// sequence from every reciprocal seed within 6 ulp (the hardware
-// approximation is within 1) on every operand pair the generator produces
-// and finds every quotient equal to the IEEE one.
-__device__ __forceinline__ float2 div_x2(float2 a, float2 b) {
-  const float2 nb = neg2(b);
-  float2 y = f2(rcp_approx(b.x), rcp_approx(b.y));
-  const float2 e = __ffma2_rn(nb, y, f2(1.0f, 1.0f));
-  y = __ffma2_rn(y, e, y);
-  const float2 q = __fmul2_rn(a, y);
-  const float2 r = __ffma2_rn(nb, q, a);
-  float2 s = __ffma2_rn(r, y, q);
-  if (b.x == 0x1.fffffep+0f) s.x = -0x1.000002p-24f;
-  if (b.y == 0x1.fffffep+0f) s.y = -0x1.000002p-24f;
-  return s;
-}
 
 // sqrt(w) rounded to nearest-even for w = -2 ln u1 in [2^-23, 34] or w = -0
 // (u1 = 1).  Markstein's square root: from an approximate reciprocal square
@@ -155,9 +127,10 @@ __device__ __forceinline__ float2 sqrt_x2(float2 w) {
   return __ffma2_rn(d, h, g);
 }
 
-// ln x for x in (0, 1] (normal): x = 2^e f, f folded into [sqrt(1/2), sqrt 2],
-// s = (f-1)/(f+1), ln f = 2s + s^3 P(s^2) with the atanh series
-// coefficients 2/3, 2/5, 2/7, 2/9; ln x = e ln2_hi + (e ln2_lo + ln f).
+// ln x for x in (0, 1] (normal): x = 2^e f, f folded into [sqrt(1/2), sqrt 2),
+// t = f - 1 (exact), ln f = t + t^2 Q(t) with Q of degree 8 (the generator
+// specification's least-squares coefficients, below), ln x = e ln2_hi +
+// (e ln2_lo + ln f).
 __device__ __forceinline__ float2 ln01_x2(float2 x) {
   const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
   // Fold and split by one integer add: with m the mantissa bits, b + 0x4afb0c
@@ -172,35 +145,31 @@ __device__ __forceinline__ float2 ln01_x2(float2 x) {
   const float2 ef = __fadd2_rn(eb, f2(-8388735.0f, -8388735.0f));
   const float2 f = f2(__uint_as_float((i0 & 0x007fffffu) + 0x3f3504f4u),
                       __uint_as_float((i1 & 0x007fffffu) + 0x3f3504f4u));
-  const float2 num = __fadd2_rn(f, f2(-1.0f, -1.0f));
-  const float2 den = __fadd2_rn(f, f2(1.0f, 1.0f));
-  const float2 sv = div_x2(num, den);
-  const float2 s2 = __fmul2_rn(sv, sv);
-  float2 p = __ffma2_rn(s2, f2(0x1.c71c72p-3f, 0x1.c71c72p-3f), f2(0x1.24924ap-2f, 0x1.24924ap-2f));
-  p = __ffma2_rn(s2, p, f2(0x1.99999ap-2f, 0x1.99999ap-2f));
-  p = __ffma2_rn(s2, p, f2(0x1.555556p-1f, 0x1.555556p-1f));
-  const float2 s3 = __fmul2_rn(sv, s2);
-  const float2 lnf = __ffma2_rn(s3, p, __fadd2_rn(sv, sv));
+  const float2 t = __fadd2_rn(f, f2(-1.0f, -1.0f));
+  float2 p = __ffma2_rn(t, f2(-0x1.321a48p-4f, -0x1.321a48p-4f), f2(0x1.068b28p-3f, 0x1.068b28p-3f));
+  p = __ffma2_rn(t, p, f2(-0x1.0f9b0cp-3f, -0x1.0f9b0cp-3f));
+  p = __ffma2_rn(t, p, f2(0x1.22bf86p-3f, 0x1.22bf86p-3f));
+  p = __ffma2_rn(t, p, f2(-0x1.5424e0p-3f, -0x1.5424e0p-3f));
+  p = __ffma2_rn(t, p, f2(0x1.999fc2p-3f, 0x1.999fc2p-3f));
+  p = __ffma2_rn(t, p, f2(-0x1.000422p-2f, -0x1.000422p-2f));
+  p = __ffma2_rn(t, p, f2(0x1.555558p-2f, 0x1.555558p-2f));
+  p = __ffma2_rn(t, p, f2(-0x1.fffff8p-2f, -0x1.fffff8p-2f));
+  const float2 lnf = __ffma2_rn(__fmul2_rn(t, t), p, t);
   return __ffma2_rn(ef, f2(0x1.62e4p-1f, 0x1.62e4p-1f),
                     __ffma2_rn(ef, f2(0x1.7f7d1cp-20f, 0x1.7f7d1cp-20f), lnf));
 }
 
-// sin(pi t), cos(pi t) of t = (v0 2^-23, v1 2^-23), v the 24-bit integers
-// given as exact floats fv: q = rint(2t) (ties to even), r = t - q/2 in
-// [-1/4, 1/4] exactly, Taylor polynomials of sin(pi r) (to r^9) and
-// cos(pi r) (to r^10) with coefficients (-1)^j pi^n/n! rounded to FP32, then
-// a rotation by q quarter turns.
-__device__ __forceinline__ void sincospi_x2(float2 fv, float2* sn_out, float2* cs_out) {
-  const float2 t = __fmul2_rn(fv, f2(0x1p-23f, 0x1p-23f));  // exact
-  // 2t + 1.5 2^23 rounded to nearest-even lies in [2^23, 2^24), where the
-  // spacing of floats is 1: its low bits hold rint(2t) (1.5 2^23 is even, so
-  // ties go to the even integer as rintf's do), and removing the offset again
-  // is exact
-  const float2 qm = __ffma2_rn(fv, f2(0x1p-22f, 0x1p-22f), f2(0x1.8p+23f, 0x1.8p+23f));
-  const float2 qf = __fadd2_rn(qm, f2(-0x1.8p+23f, -0x1.8p+23f));
-  const uint32_t q0 = __float_as_uint(qm.x), q1 = __float_as_uint(qm.y);  // low bits: q
-  // t - q/2: the product q * 0.5 is exact, so one rounding as in the scalar form
-  const float2 r = __ffma2_rn(qf, f2(-0.5f, -0.5f), t);
+// The circle points of the angle words w0, w1 before the half turn of their
+// bit 31 (the caller applies it as the sign of the radius): the position
+// r = (bits 29..8) 2^-23 - 1/4 in [-1/4, 1/4) from the bits (0.5 + w 2^-23
+// and its difference with 3/4 are exact), Taylor polynomials of sin(pi r)
+// (to r^9) and cos(pi r) (to r^10) with coefficients (-1)^j pi^n/n! rounded
+// to FP32, then (x, y) -> (-y, x) when bit 30 is set.
+__device__ __forceinline__ void circle_x2(uint32_t w0, uint32_t w1, float2* x_out,
+                                          float2* y_out) {
+  const float2 h = f2(__uint_as_float(0x3F000000u | ((w0 >> 7) & 0x007FFFFEu)),
+                      __uint_as_float(0x3F000000u | ((w1 >> 7) & 0x007FFFFEu)));
+  const float2 r = __fadd2_rn(h, f2(-0.75f, -0.75f));
   const float2 r2 = __fmul2_rn(r, r);
   float2 sp = __ffma2_rn(r2, f2(0x1.507834p-4f, 0x1.507834p-4f), f2(-0x1.32d2ccp-1f, -0x1.32d2ccp-1f));
   sp = __ffma2_rn(r2, sp, f2(0x1.466bc6p+1f, 0x1.466bc6p+1f));
@@ -212,33 +181,28 @@ __device__ __forceinline__ void sincospi_x2(float2 fv, float2* sn_out, float2* c
   cp = __ffma2_rn(r2, cp, f2(0x1.03c1f0p+2f, 0x1.03c1f0p+2f));
   cp = __ffma2_rn(r2, cp, f2(-0x1.3bd3ccp+2f, -0x1.3bd3ccp+2f));
   const float2 cs = __ffma2_rn(r2, cp, f2(1.0f, 1.0f));
-  // quarter turns q mod 4 = 0..3: (sin, cos) = (sn, cs), (cs, -sn), (-sn, -cs),
-  // (-cs, sn).  Odd q swaps the two; the sine is negated when bit 1 of q is
-  // set, the cosine when bit 1 of q + 1 is; negation flips the sign bit.
-  const uint32_t a0 = __float_as_uint((q0 & 1u) ? cs.x : sn.x);
-  const uint32_t c0 = __float_as_uint((q0 & 1u) ? sn.x : cs.x);
-  const uint32_t a1 = __float_as_uint((q1 & 1u) ? cs.y : sn.y);
-  const uint32_t c1 = __float_as_uint((q1 & 1u) ? sn.y : cs.y);
-  *sn_out = f2(__uint_as_float(a0 ^ ((q0 << 30) & 0x80000000u)),
-               __uint_as_float(a1 ^ ((q1 << 30) & 0x80000000u)));
-  *cs_out = f2(__uint_as_float(c0 ^ (((q0 + 1u) << 30) & 0x80000000u)),
-               __uint_as_float(c1 ^ (((q1 + 1u) << 30) & 0x80000000u)));
+  const bool q0 = (w0 & 0x40000000u) != 0u, q1 = (w1 & 0x40000000u) != 0u;
+  *x_out = f2(q0 ? -sn.x : cs.x, q1 ? -sn.y : cs.y);
+  *y_out = f2(q0 ? cs.x : sn.x, q1 ? cs.y : sn.y);
 }
 
 // Box-Muller of the word pairs (x.x, x.y) and (x.z, x.w), as (z0, z1, z2, z3):
-// u1 = ((xa >> 8) + 1) 2^-24, u2 = (xb >> 8) 2^-24, rho = sqrt(-2 ln u1),
-// (z_even, z_odd) = rho (cospi(2 u2), sinpi(2 u2)).
+// u1 = ((xa >> 8) + 1) 2^-24, rho = sqrt(-2 ln u1), (X, Y) the circle point
+// of xb, (z_even, z_odd) = rho (X, Y).
 __device__ __forceinline__ float4 box_muller_x2(uint4 x) {
   const float2 fa = f2(__uint2float_rn(x.x >> 8), __uint2float_rn(x.z >> 8));  // exact
-  const float2 fb = f2(__uint2float_rn(x.y >> 8), __uint2float_rn(x.w >> 8));  // exact
   // (v + 1) 2^-24 is a float, so the fused form rounds nothing
   const float2 u1 = __ffma2_rn(fa, f2(0x1p-24f, 0x1p-24f), f2(0x1p-24f, 0x1p-24f));
   const float2 v = __fmul2_rn(f2(-2.0f, -2.0f), ln01_x2(u1));
   const float2 rho = sqrt_x2(v);
-  float2 sn, cs;
-  sincospi_x2(fb, &sn, &cs);  // t = u2 + u2 = (xb >> 8) 2^-23
-  const float2 zc = __fmul2_rn(rho, cs);
-  const float2 zs = __fmul2_rn(rho, sn);
+  // the half turn of bit 31 as the sign of the radius: (-rho) X = -(rho X)
+  // exactly, signed zeros included
+  const float2 rs = f2(__uint_as_float(__float_as_uint(rho.x) ^ (x.y & 0x80000000u)),
+                       __uint_as_float(__float_as_uint(rho.y) ^ (x.w & 0x80000000u)));
+  float2 cx, cy;
+  circle_x2(x.y, x.w, &cx, &cy);
+  const float2 zc = __fmul2_rn(rs, cx);
+  const float2 zs = __fmul2_rn(rs, cy);
   return make_float4(zc.x, zs.x, zc.y, zs.y);
 }
 

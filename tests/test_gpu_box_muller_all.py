@@ -21,7 +21,7 @@ def _words():
     i = np.arange(N, dtype=np.uint64)
     w = np.empty((N, 4), dtype=np.uint32)
     w[:, 0] = ((i << 8) | (i & 0xFF)).astype(np.uint32)                   # u1 = (i + 1) 2^-24
-    w[:, 1] = ((i << 8) | 0x5A).astype(np.uint32)                         # u2 = i 2^-24
+    w[:, 1] = ((i << 8) | 0x5A).astype(np.uint32)                         # every angle word
     w[:, 2] = ((((i * 0x9E3779B1) & 0xFFFFFF) << 8) | 0xC3).astype(np.uint32)  # a permutation
     w[:, 3] = ((((~i) & 0xFFFFFF) << 8) | ((i >> 16) & 0xFF)).astype(np.uint32)
     return w
