@@ -431,11 +431,14 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, const
     }
   } else {
     // A warp covers 8 rows x 4 quads; the group covers RSTEP rows per pass.
+    // Lane l takes row l mod 8 and quad l / 8: the 16 lanes of each 128-byte
+    // phase of an 8-byte store then write both 8-byte halves of one 16-byte
+    // unit of each of 8 rows, every bank once.
     constexpr int RSTEP = C::GROUP_THREADS / 4;
     constexpr int NPASS = BM / RSTEP;
     static_assert(RSTEP % 8 == 0 && BM % RSTEP == 0, "row passes of the worker group");
-    const uint32_t qd = static_cast<uint32_t>(wt) & 3u;
-    const uint32_t rbase = static_cast<uint32_t>(wt >> 5) * 8u + ((static_cast<uint32_t>(wt) & 31u) >> 2);
+    const uint32_t qd = (static_cast<uint32_t>(wt) >> 3) & 3u;
+    const uint32_t rbase = static_cast<uint32_t>(wt >> 5) * 8u + (static_cast<uint32_t>(wt) & 7u);
     // kmaj_off(rbase + RSTEP i, qd / 2) = off0 + 32 RSTEP i (RSTEP is a multiple of 8)
     const uint32_t off0 = kmaj_off(rbase, qd >> 1) + (qd & 1u) * 8u;
     const bool full = cbase + LK <= g.lend;
@@ -1149,14 +1152,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           *reinterpret_cast<uint4*>(sdst + kmaj_off(r, hh)) = v;
         }
       } else {
-        // a lane owns quad qd of rows 16 wg + 8 it + lane / 4 (4 quads per row)
-        const uint32_t qd = static_cast<uint32_t>(lane) & 3u;
+        // a lane owns quad qd = lane / 8 of rows 16 wg + 8 it + lane % 8 (the 16
+        // lanes of a store phase write 8 rows x 16 B: every bank once)
+        const uint32_t qd = (static_cast<uint32_t>(lane) >> 3) & 3u;
         const bool cv = cbase + 4 * qd < lend;
         const uint32_t j = static_cast<uint32_t>(cbase >> 2) + qd;  // Philox block
 #pragma unroll
         for (int it = 0; it < 2; ++it) {
-          const int rr = 8 * it + (lane >> 2);
-          if (rr >= wrows) break;
+          const int rr = 8 * it + (lane & 7);
+          if (rr >= wrows) continue;
           const uint32_t r = static_cast<uint32_t>(gbase + 16 * wg + rr);
           const int64_t grow = g0 + r;
           uint2 v = make_uint2(0u, 0u);
@@ -1185,9 +1189,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       constexpr int CONV_IT = (2 * C::ROWS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
 #pragma unroll
       for (int it = 0; it < CONV_IT; ++it) {
+        // task i: row (0..255: accumulator row / 128, lane row % 128) and
+        // 8-column half hh.  The 8 lanes of a 16-byte access phase take 8
+        // consecutive rows, so their operand stores fall in 8 different
+        // 16-byte units (no conflict), with the halves alternating so that
+        // their staging reads (64-byte rows) spread over 4 bank groups.
         const int i = wt + it * C::GROUP_THREADS;
-        const int row = i >> 1;   // 0..255: accumulator row / 128, lane row % 128
-        const int hh = i & 1;
+        const int l = i & 7;
+        const int blk = i >> 3;
+        const int row = 8 * (blk >> 1) + l;
+        const int hh = ((l >> 1) & 1) ^ (blk & 1);
         const float4 x0 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh);
         const float4 x1 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh + 4);
         const float a[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
