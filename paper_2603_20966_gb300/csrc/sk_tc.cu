@@ -152,8 +152,10 @@ struct alignas(128) LeftProblem {
   int dist;         // sk_dist of S
   int chain;        // stages per TMEM accumulation chain (a power of two, multiple of 8)
   PhiloxKey key;
-  // conv_inline: the TMA brings FP32 A ({32 columns, rows, 32-column blocks},
-  // 128-byte swizzle, `amap`) and the workers split it into the BF16 halves in
+  // conv_inline: the TMA brings FP32 A as 32-column blocks of 32 rows with the
+  // 128-byte swizzle (`amap`: one 3D box of all the CTA's blocks when n is a
+  // multiple of 32 (1), else one 2D box per block (2)) and the workers split
+  // it into the BF16 halves in
   // place (single Rademacher sketches; see convert_stage); 0: the split pass
   // wrote the halves and `map` loads them
   int conv_inline;
@@ -591,7 +593,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             (DIST == kStored ? C::OPS : 0u);               // + the S tile
         const int32_t z0 =
             static_cast<int32_t>((ig.q0 + static_cast<int64_t>(rank) * ig.cols) / HCHUNK);
-        const bool conv = DIST == kRademacher && ig.pr->conv_inline;  // FP32 A, split in place
+        // FP32 A, split in place by the workers (Rademacher items on pairs)
+        const bool conv = (DIST == kRademacher || DIST == kMixed) && PAIR && ig.pr->conv_inline;
+        const int32_t x0 = static_cast<int32_t>(ig.q0 + static_cast<int64_t>(rank) * ig.cols);
         if (conv) tma_prefetch_desc(&ig.pr->amap);
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
           const int so = g % C::NSO;
@@ -600,9 +604,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (g == sc.stall_stage) continue;  // injected stall: this stage never lands
           mbar_arrive_expect_tx(full_b(so), tx);
           const int32_t y = static_cast<int32_t>(ig.lbeg + static_cast<int64_t>(s) * LK);
-          if (conv)  // FP32 A: this CTA's columns in 32-column blocks
-            tma_load_3d(sbase + C::OFF_B + so * C::OPB, &ig.pr->amap, 0, y, 2 * z0, full_b(so));
-          else
+          if (conv) {  // FP32 A: this CTA's columns as 32-column blocks of 4 KB
+            if (ig.pr->conv_inline == 1) {
+              tma_load_3d(sbase + C::OFF_B + so * C::OPB, &ig.pr->amap, 0, y, x0 / 32, full_b(so));
+            } else {
+              for (int b = 0; b < ig.cols / 32; ++b)
+                tma_load_2d(sbase + C::OFF_B + so * C::OPB + static_cast<uint32_t>(b) * 4096u,
+                             &ig.pr->amap, x0 + 32 * b, y, full_b(so));
+            }
+          } else
             tma_load_4d(sbase + C::OFF_B + so * C::OPB, map, 0, y, z0, 0, full_b(so));
           if (DIST == kStored)  // S rows p0.., columns y.. of the stage, in the operand layout
             tma_load_5d(sbase + C::OFF_S + so * C::OPS, &ig.pr->smap, 0, 0, 0,
@@ -627,7 +637,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
         // split A as loaded: [hi chunks][lo chunks] of 64 columns (4 KB each),
         // or, converted in place, [chunk][hi, lo] (8 KB per chunk)
-        const bool inl = DIST == kRademacher && ig.pr->conv_inline;
+        const bool inl = (DIST == kRademacher || DIST == kMixed) && PAIR && ig.pr->conv_inline;
         const uint32_t chunk_stride = inl ? 2 * HCHUNK_BYTES : HCHUNK_BYTES;
         const uint32_t pstride =
             inl ? HCHUNK_BYTES : static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
@@ -842,7 +852,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           stop = true;
           break;
         }
-        if constexpr (DIST == kRademacher && PAIR && !NARROW) {
+        if constexpr ((DIST == kRademacher || DIST == kMixed) && PAIR) {
           // FP32 A: split it here (the sign bits leave the workers idle)
           if (ig.pr->conv_inline)
             convert_stage<C>(smem + C::OFF_B + so * C::OPB, ig.cols, wt);
@@ -1960,34 +1970,54 @@ bool encode_stored_map(CUtensorMap* map, const void* S, int64_t k, int64_t m, in
 // Rademacher sketches drain the accumulator half as often as the others.
 int left_chain_stages(int dist) { return dist == kRademacher ? 2 * CHAIN_L : CHAIN_L; }
 
-// FP32 A[m x n] (row stride lda, n a multiple of 32) as a 3D tensor {32
-// columns, m rows, n / 32 blocks of 32 columns}: one box = `cols` columns of
-// 32 rows, as blocks [block][32 rows][32 floats] with the 128-byte swizzle.
-bool encode_fp32_blocks_map(CUtensorMap* map, const float* A, int64_t m, int64_t n, int64_t lda,
-                            int cols) {
+// FP32 A[m x n] (row stride lda) for the in-place split, as 32-column blocks
+// [32 rows][32 floats] with the 128-byte swizzle in shared memory; rows past
+// m read as zeros.  With n a multiple of 32, a 3D tensor {32 columns, m rows,
+// n / 32 blocks} whose one box holds all `cols` columns of a CTA (blocks past
+// n read as zeros); otherwise a 2D tensor {n, m} with one 32 x 32 box per
+// block (columns past n read as zeros: a 3D box would read the start of the
+// next row there).  One box per stage is the faster (C2 Rademacher 2.60 ms
+// against 2.82 ms with 8 boxes).  The TMA needs A 16-byte aligned and lda a
+// multiple of 4 (fp32_map_ok).  Returns the conv_inline mode, 0 on failure.
+bool fp32_map_ok(const float* A, int64_t lda) {
+  return reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0;
+}
+int encode_fp32_map(CUtensorMap* map, const float* A, int64_t m, int64_t n, int64_t lda,
+                    int cols) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (enc == nullptr) return false;
-  const cuuint64_t gdim[3] = {32, static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n / 32)};
-  const cuuint64_t gstride[2] = {static_cast<cuuint64_t>(lda) * 4, 128};
-  const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(LK), static_cast<cuuint32_t>(cols / 32)};
-  const cuuint32_t estride[3] = {1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(A), gdim, gstride, box,
+  if (enc == nullptr) return 0;
+  if (n % 32 == 0) {
+    const cuuint64_t gdim[3] = {32, static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n / 32)};
+    const cuuint64_t gstride[2] = {static_cast<cuuint64_t>(lda) * 4, 128};
+    const cuuint32_t box[3] = {32, static_cast<cuuint32_t>(LK), static_cast<cuuint32_t>(cols / 32)};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(A), gdim, gstride,
+               box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS ? 1 : 0;
+  }
+  const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(m)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(lda) * 4};
+  const cuuint32_t box[2] = {32, static_cast<cuuint32_t>(LK)};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim, gstride, box,
              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS ? 2 : 0;
 }
 
 // A_inline: FP32 A (row stride lda) that the kernel splits in place instead
-// of reading the split pass's halves from H (Rademacher pair sketches with n
-// a multiple of 32), or null.
+// of reading the split pass's halves from H (Rademacher problems on CTA
+// pairs, A passing fp32_map_ok), or null.
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
                   float* part, uint64_t seed, int dist, const float* A_inline = nullptr,
                   int64_t lda = 0) {
   memset(pr, 0, sizeof(*pr));
   if (!encode_split_map(&pr->map, H, s.L, s.Q, pl.pair ? pl.nt / 2 : pl.nt)) return false;
   if (A_inline != nullptr) {
-    if (!encode_fp32_blocks_map(&pr->amap, A_inline, s.L, s.Q, lda, pl.pair ? pl.nt / 2 : pl.nt))
-      return false;
-    pr->conv_inline = 1;
+    if (!pl.pair) return false;
+    pr->conv_inline = encode_fp32_map(&pr->amap, A_inline, s.L, s.Q, lda, pl.nt / 2);
+    if (pr->conv_inline == 0) return false;
   }
   pr->part = part;
   pr->P = s.P;
@@ -2356,7 +2386,8 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
   hs.probs.resize(1);
   // Rademacher pair sketches split A inside the kernel (their workers are
   // otherwise idle); the others read the halves the split pass writes
-  const bool conv = S_stored == nullptr && h->dist == kRademacher && pl.pair && s.Q % 32 == 0;
+  const bool conv =
+      S_stored == nullptr && h->dist == kRademacher && pl.pair && fp32_map_ok(A, lda);
   if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist, conv ? A : nullptr, lda))
     return cudaErrorInvalidValue;
   if (S_stored && !encode_stored_map(&hs.probs[0].smap, S_stored, s.P, s.L, lds))
@@ -2463,9 +2494,15 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
     const BatchMember& mb = mbs[i];
     uint8_t* w = mb.ws ? static_cast<uint8_t*>(mb.ws) : arena + ws_off[i];
     float* part = reinterpret_cast<float*>(w + split_bytes(mb.m, mb.n));
-    if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], w, part, mb.seed, mb.dist))
+    // Rademacher members split A inside the sketch kernel (their workers are
+    // otherwise idle); the others (and members whose split is already made)
+    // read the halves
+    const bool conv = !mb.split_ready && mb.dist == kRademacher && plans[i].pair &&
+                      fp32_map_ok(mb.A, mb.lda);
+    if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], w, part, mb.seed, mb.dist,
+                      conv ? mb.A : nullptr, mb.lda))
       return false;
-    if (!mb.split_ready) {
+    if (!mb.split_ready && !conv) {
       SplitDesc d;
       d.A = mb.A;
       d.lda = mb.lda;
