@@ -218,11 +218,13 @@ def oracle_sample(m, n, k, dists, a_part, seed, rows, nthreads=None, side="left"
 
 
 def generator_floor(dist: int, entries: float, sm_mhz: float, sms: int):
-    """Issue-rate floor of generating `entries` entries of S: the generator's
-    thread instructions per entry (from the committed ncu summary of the left
-    kernel, or None when that kernel's source changed since) over the issue
-    rate of every SM (4 schedulers x 32 lanes per cycle).  Returns (ms,
-    instructions per entry) or None."""
+    """Issue-rate floor of the Gaussian sketch kernel, which generation
+    bounds: its thread instructions (every role) per generated entry of S,
+    from the committed ncu summary of the left kernel (None when that
+    kernel's source changed since), over the issue rate of every SM (4
+    schedulers x 32 lanes per cycle) -- the kernel's time if it issued an
+    instruction on every scheduler in every cycle.  Returns (ms, instructions
+    per entry) or None."""
     if dist != 0:
         return None  # sign bits: one Philox word per 32 entries, not separable
     prof = os.path.join(ROOT, "profiles", "k_sketch_bf16x2_left_pair_m2e18.md")
@@ -231,7 +233,7 @@ def generator_floor(dist: int, entries: float, sm_mhz: float, sms: int):
         text = open(prof).read()
     except OSError:
         return None
-    key = "gaussian_thread_instructions_per_entry"
+    key = "gaussian_kernel_thread_instructions_per_entry"
     rec = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and
                line.split(": ", 1)[0] in ("left_kernel_source_sha256_16", key))
     if sha is None or rec.get("left_kernel_source_sha256_16") != sha or key not in rec:
@@ -878,9 +880,9 @@ def run_ours(args):
                                       if floors else None)
         if floors:
             roof["generator_floor_note"] = (
-                "entries x the generator's thread instructions per entry (committed ncu "
-                "summary of this kernel source) / (SMs x 128 issue lanes x median SM clock): "
-                f"{floors}")
+                "entries x the Gaussian kernel's thread instructions per generated entry "
+                "(every role; committed ncu summary of this kernel source) / (SMs x 128 issue "
+                f"lanes x median SM clock): its time at full issue, {floors}")
     serve = None
     if (args.workload == "C2" and args.rows is None and args.serve_leg_requests > 0 and
             not args.split):
