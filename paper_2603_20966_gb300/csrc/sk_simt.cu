@@ -14,11 +14,26 @@
 namespace sk {
 namespace {
 
-constexpr int BP = 128;  // output rows per CTA
-constexpr int BQ = 128;  // output cols per CTA
-constexpr int BL = 32;   // contracted length per stage
-constexpr int TPB = 256; // 16 x 16 threads, 8 x 8 outputs each
-constexpr int PAD = 4;
+constexpr int BL = 16;    // contracted length per stage
+constexpr int TPB = 256;  // 16 x 16 threads
+
+// Tile of Y per CTA: BP rows x BQ columns, a TM x TN micro-tile per thread
+// (TM = BP / 16, TN = BQ / 16).  The left form (Y = S A) takes 128 rows of k
+// and 256 columns of n, the right form (Y = A S^T) 256 rows of m and 128
+// rows of k: each generated entry of S serves 256 columns (left) or rows
+// (right) of A, and per stage a CTA generates 2048 entries for 32768 FMAs.
+template <bool LEFT>
+struct SimtTile {
+  static constexpr int BP = LEFT ? 128 : 256;
+  static constexpr int BQ = LEFT ? 256 : 128;
+  static constexpr int TM = BP / 16, TN = BQ / 16;
+  // X (the BP side) is stored with every value twice, X2[l][2r] =
+  // X2[l][2r+1] = X[l][r], so that one 16-byte load gives two (x, x) pairs for
+  // the packed FMAs; W (the BQ side) as is
+  static constexpr int XW = 2 * BP;
+  static constexpr int STAGE = BL * (XW + BQ);  // floats per stage buffer
+  static constexpr size_t SMEM = 2 * STAGE * sizeof(float);
+};
 
 struct SimtParams {
   const float* A;
@@ -27,121 +42,215 @@ struct SimtParams {
   int64_t ldo;
   int64_t P, Q, L;
   int64_t chunk;    // contracted length per split (multiple of BL)
-  PhiloxKey key;
+  PhiloxRoundKeys rk;
   int dist;
   float scale;      // applied only when splits == 1
   int splits;
+  int vec;          // A 16-byte aligned and lda a multiple of 4: 16-byte loads
 };
 
-// Generated operand tile: G[l][t] = g(t0 + t, l0 + l) for t < BT (generated
-// row index = sketch row), l < BL.  Zero outside the matrix.
-template <int BT>
-__device__ __forceinline__ void gen_tile(float (*G)[BT + PAD], const SimtParams& p, int64_t t0,
-                                         int64_t tmax, int64_t l0) {
-  // BT rows x (BL/4) groups of 4 columns
-  for (int idx = threadIdx.x; idx < BT * (BL / 4); idx += TPB) {
-    const int t = idx % BT;
-    const int j = idx / BT;
+// Four consecutive generated values (r, c0 .. c0+3), c0 % 4 == 0, unquantized.
+__device__ __forceinline__ float4 gen4_rk(int dist, const PhiloxRoundKeys& rk, uint32_t r,
+                                          uint32_t c0) {
+  if (dist == kRademacher) {
+    const uint4 x = rademacher_bits(rk, r, c0 >> 7, 0u);
+    const uint32_t wsel = (c0 >> 5) & 3u;
+    const uint32_t w = wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w;
+    const uint32_t bits = w >> (c0 & 31u);
+    return make_float4((bits & 1u) ? -1.f : 1.f, (bits & 2u) ? -1.f : 1.f,
+                       (bits & 4u) ? -1.f : 1.f, (bits & 8u) ? -1.f : 1.f);
+  }
+  if (dist == kUniform) return uniform4(rk, r, c0 >> 2, 0u);
+  return gaussian4(rk, r, c0 >> 2, 0u);
+}
+
+// The generated values (t0 + t, l0 + l) of a stage, t < BT, l < BL, zero
+// past tmax rows or past lend, in 2 x 256 tasks of one row t and 4
+// consecutive l; this is the calling thread's task u (0 or 1).  Lanes of a
+// warp take consecutive rows (conflict-free shared stores).  DUP: stored
+// twice at X2[l][2t], X2[l][2t+1] (the X side); else at W[l][t].
+template <int BT, bool DUP>
+__device__ __forceinline__ void gen_task_fp32(float* buf, const SimtParams& p, int64_t t0,
+                                              int64_t tmax, int64_t l0, int64_t lend, int u) {
+  static_assert(BT * (BL / 4) == 2 * TPB, "two generation tasks per thread and stage");
+  {
+    const int task = static_cast<int>(threadIdx.x) + TPB * u;
+    const int t = task % BT;
+    const int jg = task / BT;
     const int64_t r = t0 + t;
-    const int64_t c = l0 + 4 * j;
+    const int64_t c = l0 + 4 * jg;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < tmax && c < p.L) {
-      v = gen4(p.dist, p.key, (uint32_t)r, (uint32_t)c, 0u);
-      if (c + 1 >= p.L) v.y = 0.f;
-      if (c + 2 >= p.L) v.z = 0.f;
-      if (c + 3 >= p.L) v.w = 0.f;
+    if (r < tmax && c < lend) {
+      v = gen4_rk(p.dist, p.rk, static_cast<uint32_t>(r), static_cast<uint32_t>(c));
+      if (c + 1 >= lend) v.y = 0.f;
+      if (c + 2 >= lend) v.z = 0.f;
+      if (c + 3 >= lend) v.w = 0.f;
     }
-    G[4 * j + 0][t] = v.x;
-    G[4 * j + 1][t] = v.y;
-    G[4 * j + 2][t] = v.z;
-    G[4 * j + 3][t] = v.w;
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (DUP)
+        *reinterpret_cast<float2*>(buf + (4 * jg + i) * (2 * BT) + 2 * t) = make_float2(vv[i], vv[i]);
+      else
+        buf[(4 * jg + i) * BT + t] = vv[i];
+    }
+  }
+}
+
+// Four 4-element pieces of A per thread for the stage at l0.  Left: the W
+// tile A[l0 + l][q0 + q] (l < 16, q < 256: piece f = tid + 256 u is row
+// f / 64, columns 4 (f % 64) ..); right: the X tile A[p0 + r][l0 + l] (row
+// r = tid, columns 4u ..).  Zero outside the matrix and past lend.
+template <bool LEFT>
+__device__ __forceinline__ void load_a(float4 (&pa)[4], const SimtParams& p, int64_t p0,
+                                       int64_t q0, int64_t l0, int64_t lend) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int f = static_cast<int>(threadIdx.x) + TPB * u;
+    int64_t row, col, col_end;  // the piece is A[row][col .. col + 3]
+    bool row_ok;
+    if (LEFT) {
+      row = l0 + f / 64;
+      col = q0 + 4 * (f % 64);
+      row_ok = row < lend;
+      col_end = p.Q;
+    } else {
+      row = p0 + static_cast<int>(threadIdx.x);
+      col = l0 + 4 * u;
+      row_ok = row < p.P;
+      col_end = lend;
+    }
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row_ok) {
+      const float* src = p.A + row * p.lda + col;
+      if (p.vec && col + 3 < col_end) {
+        v = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        if (col < col_end) v.x = __ldg(src);
+        if (col + 1 < col_end) v.y = __ldg(src + 1);
+        if (col + 2 < col_end) v.z = __ldg(src + 2);
+        if (col + 3 < col_end) v.w = __ldg(src + 3);
+      }
+    }
+    pa[u] = v;
   }
 }
 
 template <bool LEFT>
-__global__ void __launch_bounds__(TPB) k_sketch_fp32_simt(SimtParams p) {
-  __shared__ __align__(16) float Xs[BL][BP + PAD];
-  __shared__ __align__(16) float Ws[BL][BQ + PAD];
+__device__ __forceinline__ void store_a(float* buf, const float4 (&pa)[4]) {
+  using T = SimtTile<LEFT>;
+  float* xs = buf;
+  float* ws = buf + BL * T::XW;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int f = static_cast<int>(threadIdx.x) + TPB * u;
+    if (LEFT) {  // W[l][q], l = f / 64, q = 4 (f % 64)
+      *reinterpret_cast<float4*>(ws + (f / 64) * T::BQ + 4 * (f % 64)) = pa[u];
+    } else {     // X2[l][2r], r = tid, l = 4u .. 4u+3
+      const int r = static_cast<int>(threadIdx.x);
+      const float vv[4] = {pa[u].x, pa[u].y, pa[u].z, pa[u].w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float2*>(xs + (4 * u + i) * T::XW + 2 * r) = make_float2(vv[i], vv[i]);
+    }
+  }
+}
+
+// Y tile = sum over l of X[l][rows] (outer) W[l][cols], FP32 FMA: the local
+// multiply of Alg. 1 with the random operand generated into shared memory
+// stage by stage (double-buffered: the next stage's A is loaded into
+// registers before, and its S tile generated after, the current stage's
+// FMAs).  Packed FP32x2 FMAs (__ffma2_rn: each component the correctly
+// rounded fmaf) update two columns of a row per instruction.
+template <bool LEFT>
+__global__ void __launch_bounds__(TPB, 1) k_sketch_fp32_simt(SimtParams p) {
+  using T = SimtTile<LEFT>;
+  extern __shared__ __align__(16) float smem_f[];
   // the tiles along the long side (n of the left sketch, m of the right) run
   // along grid x, whose extent is not limited to 65535
-  const int64_t q0 = (int64_t)(LEFT ? blockIdx.x : blockIdx.y) * BQ;
-  const int64_t p0 = (int64_t)(LEFT ? blockIdx.y : blockIdx.x) * BP;
+  const int64_t q0 = (int64_t)(LEFT ? blockIdx.x : blockIdx.y) * T::BQ;
+  const int64_t p0 = (int64_t)(LEFT ? blockIdx.y : blockIdx.x) * T::BP;
   const int64_t lbeg = (int64_t)blockIdx.z * p.chunk;
   const int64_t lend = min(p.L, lbeg + p.chunk);
+  const int nst = static_cast<int>((lend - lbeg + BL - 1) / BL);
   const int tq = threadIdx.x % 16;
   const int tp = threadIdx.x / 16;
 
-  float acc[8][8];
+  float2 acc[T::TM][T::TN / 2];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < T::TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < T::TN / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  for (int64_t l0 = lbeg; l0 < lend; l0 += BL) {
-    if (LEFT) {
-      gen_tile<BP>(Xs, p, p0, p.P, l0);
-      // W(l, q) = A[l][q]: rows of A, coalesced along q
-      for (int idx = threadIdx.x; idx < BL * BQ; idx += TPB) {
-        const int l = idx / BQ, q = idx % BQ;
-        const int64_t gl = l0 + l, gq = q0 + q;
-        Ws[l][q] = (gl < lend && gq < p.Q) ? __ldg(p.A + gl * p.lda + gq) : 0.f;
-      }
-    } else {
-      gen_tile<BQ>(Ws, p, q0, p.Q, l0);
-      // X(p, l) = A[p][l]: coalesced along l, stored transposed
-      for (int idx = threadIdx.x; idx < BL * BP; idx += TPB) {
-        const int l = idx % BL, r = idx / BL;
-        const int64_t gl = l0 + l, gp = p0 + r;
-        Xs[l][r] = (gl < lend && gp < p.P) ? __ldg(p.A + gp * p.lda + gl) : 0.f;
-      }
-    }
-    if (LEFT) {
-      // the generated tile may extend past this split's range: zero it
-      if (l0 + BL > lend) {
-        for (int idx = threadIdx.x; idx < BL * BP; idx += TPB) {
-          const int l = idx / BP, r = idx % BP;
-          if (l0 + l >= lend) Xs[l][r] = 0.f;
-        }
-      }
-    } else if (l0 + BL > lend) {
-      for (int idx = threadIdx.x; idx < BL * BQ; idx += TPB) {
-        const int l = idx / BQ, q = idx % BQ;
-        if (l0 + l >= lend) Ws[l][q] = 0.f;
-      }
-    }
-    __syncthreads();
-#pragma unroll 4
+  // generation task u (of 2) of the stage at l0 into buffer buf
+  auto gen = [&](float* buf, int64_t l0, int u) {
+    if constexpr (LEFT)
+      gen_task_fp32<T::BP, true>(buf, p, p0, p.P, l0, lend, u);
+    else
+      gen_task_fp32<T::BQ, false>(buf + BL * T::XW, p, q0, p.Q, l0, lend, u);
+  };
+
+  float4 pa[4];
+  if (nst > 0) {
+    load_a<LEFT>(pa, p, p0, q0, lbeg, lend);
+    gen(smem_f, lbeg, 0);
+    gen(smem_f, lbeg, 1);
+    store_a<LEFT>(smem_f, pa);
+  }
+  __syncthreads();
+  for (int st = 0; st < nst; ++st) {
+    const int64_t l0 = lbeg + static_cast<int64_t>(st) * BL;
+    const bool more = st + 1 < nst;
+    float* next = smem_f + ((st + 1) & 1) * T::STAGE;
+    if (more) load_a<LEFT>(pa, p, p0, q0, l0 + BL, lend);
+    const float* xs = smem_f + (st & 1) * T::STAGE;
+    const float* ws = xs + BL * T::XW;
+#pragma unroll 2
     for (int l = 0; l < BL; ++l) {
-      float xr[8], wr[8];
-      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[l][tp * 4]);
-      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[l][64 + tp * 4]);
-      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[l][tq * 4]);
-      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[l][64 + tq * 4]);
-      xr[0] = x0.x; xr[1] = x0.y; xr[2] = x0.z; xr[3] = x0.w;
-      xr[4] = x1.x; xr[5] = x1.y; xr[6] = x1.z; xr[7] = x1.w;
-      wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
-      wr[4] = w1.x; wr[5] = w1.y; wr[6] = w1.z; wr[7] = w1.w;
+      // the next stage's S tile is generated between this stage's FMAs (it
+      // goes to the other buffer), so generation and FMAs share the cycles
+      if (more && (l == 2 || l == 9)) gen(next, l0 + BL, l == 2 ? 0 : 1);
+      float2 xr[T::TM];
+      float2 wr[T::TN / 2];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int a = 0; a < T::TM / 4; ++a) {
+        const float* src = xs + l * T::XW + 2 * (64 * a + 4 * tp);
+        const float4 u0 = *reinterpret_cast<const float4*>(src);
+        const float4 u1 = *reinterpret_cast<const float4*>(src + 4);
+        xr[4 * a + 0] = make_float2(u0.x, u0.y);
+        xr[4 * a + 1] = make_float2(u0.z, u0.w);
+        xr[4 * a + 2] = make_float2(u1.x, u1.y);
+        xr[4 * a + 3] = make_float2(u1.z, u1.w);
+      }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xr[i], wr[j], acc[i][j]);
+      for (int b = 0; b < T::TN / 4; ++b) {
+        const float4 w = *reinterpret_cast<const float4*>(ws + l * T::BQ + 64 * b + 4 * tq);
+        wr[2 * b] = make_float2(w.x, w.y);
+        wr[2 * b + 1] = make_float2(w.z, w.w);
+      }
+#pragma unroll
+      for (int i = 0; i < T::TM; ++i)
+#pragma unroll
+        for (int j = 0; j < T::TN / 2; ++j) acc[i][j] = __ffma2_rn(xr[i], wr[j], acc[i][j]);
     }
+    if (more) store_a<LEFT>(next, pa);
     __syncthreads();
   }
 
-  // rows p0 + {tp*4 .. tp*4+3, 64+tp*4 ..}, cols q0 + {tq*4 .., 64+tq*4 ..}
+  // acc[4a + i][2b + jj]: row p0 + 64a + 4tp + i, columns q0 + 64b + 4tq + 2jj (+1)
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t gp = p0 + (i < 4 ? tp * 4 + i : 64 + tp * 4 + (i - 4));
+  for (int i = 0; i < T::TM; ++i) {
+    const int64_t gp = p0 + 64 * (i / 4) + 4 * tp + (i % 4);
     if (gp >= p.P) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t gq = q0 + (j < 4 ? tq * 4 + j : 64 + tq * 4 + (j - 4));
+    for (int j = 0; j < T::TN; ++j) {
+      const int64_t gq = q0 + 64 * (j / 4) + 4 * tq + (j % 4);
       if (gq >= p.Q) continue;
+      const float v = (j & 1) ? acc[i][j / 2].y : acc[i][j / 2].x;
       if (p.splits == 1) {
-        p.out[gp * p.ldo + gq] = __fmul_rn(p.scale, acc[i][j]);
+        p.out[gp * p.ldo + gq] = __fmul_rn(p.scale, v);
       } else {
-        p.out[((int64_t)blockIdx.z * p.P + gp) * p.Q + gq] = acc[i][j];
+        p.out[((int64_t)blockIdx.z * p.P + gp) * p.Q + gq] = v;
       }
     }
   }
@@ -194,6 +303,22 @@ __global__ void k_materialize(PhiloxKey key, int dist, int fmt, int scaled, floa
   }
 }
 
+// The FP32 kernels' dynamic shared memory (two stage buffers: 64 / 80 KB)
+// is above the 48 KB default: allowed once per process.
+cudaError_t set_simt_smem() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_fp32_simt<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(SimtTile<true>::SMEM));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_fp32_simt<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(SimtTile<false>::SMEM));
+  done = e == cudaSuccess;
+  return e;
+}
+
 int num_sms() {
   static int sms = 0;
   if (sms == 0) {
@@ -206,13 +331,30 @@ int num_sms() {
 }
 
 void plan_splits(const GemmShape& s, int* splits, int64_t* chunk) {
-  const int64_t tiles = ((s.P + BP - 1) / BP) * ((s.Q + BQ - 1) / BQ);
-  const int64_t target = 3LL * num_sms();
-  int64_t sp = (target + tiles - 1) / tiles;
-  const int64_t max_sp = s.L / (4 * BL) > 0 ? s.L / (4 * BL) : 1;
-  if (sp > max_sp) sp = max_sp;
-  if (sp > 64) sp = 64;
-  if (sp < 1) sp = 1;
+  const int bp = s.left ? SimtTile<true>::BP : SimtTile<false>::BP;
+  const int bq = s.left ? SimtTile<true>::BQ : SimtTile<false>::BQ;
+  const int64_t tiles = ((s.P + bp - 1) / bp) * ((s.Q + bq - 1) / bq);
+  const int64_t sms = num_sms();  // one CTA per SM (registers, shared memory)
+  int64_t max_sp = s.L / (8 * BL) > 0 ? s.L / (8 * BL) : 1;
+  if (max_sp > 64) max_sp = 64;
+  // the fewest splits with at least two waves of CTAs whose last wave is
+  // nearly full (>= 90 % of the SMs busy over the whole launch), else the
+  // best-filled count up to 8 waves
+  int64_t sp = 1;
+  double best = -1.0;
+  for (int64_t c = 1; c <= max_sp; ++c) {
+    const int64_t ctas = tiles * c;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    const double fill = static_cast<double>(ctas) / static_cast<double>(waves * sms);
+    if (ctas >= 2 * sms && fill >= 0.9) {
+      sp = c;
+      break;
+    }
+    if (waves <= 8 && fill > best + 1e-9) {
+      best = fill;
+      sp = c;
+    }
+  }
   int64_t ch = (s.L + sp - 1) / sp;
   ch = (ch + BL - 1) / BL * BL;
   sp = (s.L + ch - 1) / ch;
@@ -264,10 +406,11 @@ cudaError_t simt_sketch(const sk_sketch* h, const GemmShape& s, const float* A, 
   p.Q = s.Q;
   p.L = s.L;
   p.chunk = chunk;
-  p.key = make_key(h->seed);
+  p.rk = round_keys(make_key(h->seed));
   p.dist = h->dist;
   p.scale = h->scale;
   p.splits = splits;
+  p.vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
   if (splits > 1) {
     if (ws == nullptr || ws_bytes < simt_workspace_bytes(s)) return cudaErrorInvalidValue;
     p.out = static_cast<float*>(ws);
@@ -278,16 +421,20 @@ cudaError_t simt_sketch(const sk_sketch* h, const GemmShape& s, const float* A, 
   }
   // grid x: tiles of the long side (n or m); grid y: tiles of k, at most
   // 65535 (k <= 8,388,480 in this form; a larger k fails the launch)
-  const unsigned tq = (unsigned)((s.Q + BQ - 1) / BQ), tp = (unsigned)((s.P + BP - 1) / BP);
+  const int bp = s.left ? SimtTile<true>::BP : SimtTile<false>::BP;
+  const int bq = s.left ? SimtTile<true>::BQ : SimtTile<false>::BQ;
+  const unsigned tq = (unsigned)((s.Q + bq - 1) / bq), tp = (unsigned)((s.P + bp - 1) / bp);
   dim3 grid(s.left ? tq : tp, s.left ? tp : tq, (unsigned)splits);
+  cudaError_t e = set_simt_smem();
+  if (e != cudaSuccess) return e;
   prof_mark(h->prof_start, st);
   if (s.left)
-    k_sketch_fp32_simt<true><<<grid, TPB, 0, st>>>(p);
+    k_sketch_fp32_simt<true><<<grid, TPB, SimtTile<true>::SMEM, st>>>(p);
   else
-    k_sketch_fp32_simt<false><<<grid, TPB, 0, st>>>(p);
+    k_sketch_fp32_simt<false><<<grid, TPB, SimtTile<false>::SMEM, st>>>(p);
   prof_mark(h->prof_stop, st);
   count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   return splitk_reduce(static_cast<float*>(ws), splits, s.P, s.Q, h->scale, Y, ldy, st);
 }
