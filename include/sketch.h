@@ -106,9 +106,10 @@ sk_status sk_get_info(sk_handle h, uint64_t* seed, int* dist, int64_t* k, int* p
  * for r < k, c < m.  Requires m < 2^32.  The tensor-core forms additionally
  * require A and Y 16-byte aligned and lda, ldy multiples of 4 (SK_EINVAL
  * otherwise).  Y is fully overwritten.  A and Y must not overlap.
- * In the SK_FP32 form k is at most 8,388,480 (65535 launch tiles of 128
- * rows of S); CUDA rejects the launch of a larger k and the call returns
- * SK_ECUDA (nothing runs). */
+ * In the SK_FP32 form k is at most 65535 launch tiles of rows of S: 8,388,480
+ * when n > 128 (tiles of 128 rows), 16,776,960 when n <= 128 (tiles of 256
+ * rows); CUDA rejects the launch of a larger k and the call returns SK_ECUDA
+ * (nothing runs). */
 sk_status sk_apply_left(sk_handle h, const float* A, int64_t m, int64_t n, int64_t lda, float* Y,
                         int64_t ldy, void* stream);
 

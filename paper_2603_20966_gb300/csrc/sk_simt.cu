@@ -18,15 +18,21 @@ constexpr int BL = 16;    // contracted length per stage
 constexpr int TPB = 256;  // 16 x 16 threads
 
 // Tile of Y per CTA: BP rows x BQ columns, a TM x TN micro-tile per thread
-// (TM = BP / 16, TN = BQ / 16).  The left form (Y = S A) takes 128 rows of k
-// and 256 columns of n, the right form (Y = A S^T) 256 rows of m and 128
-// rows of k: each generated entry of S serves 256 columns (left) or rows
-// (right) of A, and per stage a CTA generates 2048 entries for 32768 FMAs.
-template <bool LEFT>
+// (TM = BP / 16, TN = BQ / 16).  The wide left tile (Y = S A, n > 128) takes
+// 128 rows of k and 256 columns of n, so that each generated entry of S
+// serves 256 columns of A; the narrow left tile (n <= 128) 256 rows of k and
+// 128 columns of n, so that few of its columns are past n; the right tile
+// (Y = A S^T) 256 rows of m and 128 rows of k.  A stage is 32768 FMAs.
+template <bool LEFT, bool WIDE>
 struct SimtTile {
-  static constexpr int BP = LEFT ? 128 : 256;
-  static constexpr int BQ = LEFT ? 256 : 128;
+  static constexpr int BP = LEFT && WIDE ? 128 : 256;
+  static constexpr int BQ = LEFT && WIDE ? 256 : 128;
   static constexpr int TM = BP / 16, TN = BQ / 16;
+  // the generated side (X for the left form, W for the right) and its
+  // generation tasks per thread and stage (one row, 4 values each)
+  static constexpr int GT = (LEFT ? BP : BQ) * (BL / 4) / TPB;
+  // 16-byte pieces of A per thread and stage
+  static constexpr int NA = LEFT ? BL * BQ / 4 / TPB : BP * BL / 4 / TPB;
   // X (the BP side) is stored with every value twice, X2[l][2r] =
   // X2[l][2r+1] = X[l][r], so that one 16-byte load gives two (x, x) pairs for
   // the packed FMAs; W (the BQ side) as is
@@ -65,14 +71,14 @@ __device__ __forceinline__ float4 gen4_rk(int dist, const PhiloxRoundKeys& rk, u
 }
 
 // The generated values (t0 + t, l0 + l) of a stage, t < BT, l < BL, zero
-// past tmax rows or past lend, in 2 x 256 tasks of one row t and 4
-// consecutive l; this is the calling thread's task u (0 or 1).  Lanes of a
+// past tmax rows or past lend, in BT x 4 tasks of one row t and 4
+// consecutive l; this is the calling thread's task u (of BT / 64).  Lanes of a
 // warp take consecutive rows (conflict-free shared stores).  DUP: stored
 // twice at X2[l][2t], X2[l][2t+1] (the X side); else at W[l][t].
 template <int BT, bool DUP>
 __device__ __forceinline__ void gen_task_fp32(float* buf, const SimtParams& p, int64_t t0,
                                               int64_t tmax, int64_t l0, int64_t lend, int u) {
-  static_assert(BT * (BL / 4) == 2 * TPB, "two generation tasks per thread and stage");
+  static_assert(BT * (BL / 4) % TPB == 0, "whole generation tasks per thread and stage");
   {
     const int task = static_cast<int>(threadIdx.x) + TPB * u;
     const int t = task % BT;
@@ -97,21 +103,24 @@ __device__ __forceinline__ void gen_task_fp32(float* buf, const SimtParams& p, i
   }
 }
 
-// Four 4-element pieces of A per thread for the stage at l0.  Left: the W
-// tile A[l0 + l][q0 + q] (l < 16, q < 256: piece f = tid + 256 u is row
-// f / 64, columns 4 (f % 64) ..); right: the X tile A[p0 + r][l0 + l] (row
-// r = tid, columns 4u ..).  Zero outside the matrix and past lend.
-template <bool LEFT>
+// The NA 4-element pieces of A per thread for the stage at l0.  Left: the W
+// tile A[l0 + l][q0 + q] (l < 16, q < BQ: piece f = tid + 256 u is row
+// f / (BQ / 4), columns 4 (f % (BQ / 4)) ..); right: the X tile
+// A[p0 + r][l0 + l] (row r = tid, columns 4u ..).  Zero outside the matrix
+// and past lend.
+template <bool LEFT, bool WIDE>
 __device__ __forceinline__ void load_a(float4 (&pa)[4], const SimtParams& p, int64_t p0,
                                        int64_t q0, int64_t l0, int64_t lend) {
+  using T = SimtTile<LEFT, WIDE>;
+  constexpr int QP = T::BQ / 4;  // pieces per row of the left W tile
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < T::NA; ++u) {
     const int f = static_cast<int>(threadIdx.x) + TPB * u;
     int64_t row, col, col_end;  // the piece is A[row][col .. col + 3]
     bool row_ok;
     if (LEFT) {
-      row = l0 + f / 64;
-      col = q0 + 4 * (f % 64);
+      row = l0 + f / QP;
+      col = q0 + 4 * (f % QP);
       row_ok = row < lend;
       col_end = p.Q;
     } else {
@@ -136,16 +145,17 @@ __device__ __forceinline__ void load_a(float4 (&pa)[4], const SimtParams& p, int
   }
 }
 
-template <bool LEFT>
+template <bool LEFT, bool WIDE>
 __device__ __forceinline__ void store_a(float* buf, const float4 (&pa)[4]) {
-  using T = SimtTile<LEFT>;
+  using T = SimtTile<LEFT, WIDE>;
+  constexpr int QP = T::BQ / 4;
   float* xs = buf;
   float* ws = buf + BL * T::XW;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < T::NA; ++u) {
     const int f = static_cast<int>(threadIdx.x) + TPB * u;
-    if (LEFT) {  // W[l][q], l = f / 64, q = 4 (f % 64)
-      *reinterpret_cast<float4*>(ws + (f / 64) * T::BQ + 4 * (f % 64)) = pa[u];
+    if (LEFT) {  // W[l][q], l = f / QP, q = 4 (f % QP)
+      *reinterpret_cast<float4*>(ws + (f / QP) * T::BQ + 4 * (f % QP)) = pa[u];
     } else {     // X2[l][2r], r = tid, l = 4u .. 4u+3
       const int r = static_cast<int>(threadIdx.x);
       const float vv[4] = {pa[u].x, pa[u].y, pa[u].z, pa[u].w};
@@ -162,9 +172,9 @@ __device__ __forceinline__ void store_a(float* buf, const float4 (&pa)[4]) {
 // registers before, and its S tile generated after, the current stage's
 // FMAs).  Packed FP32x2 FMAs (__ffma2_rn: each component the correctly
 // rounded fmaf) update two columns of a row per instruction.
-template <bool LEFT>
+template <bool LEFT, bool WIDE>
 __global__ void __launch_bounds__(TPB, 1) k_sketch_fp32_simt(SimtParams p) {
-  using T = SimtTile<LEFT>;
+  using T = SimtTile<LEFT, WIDE>;
   extern __shared__ __align__(16) float smem_f[];
   // the tiles along the long side (n of the left sketch, m of the right) run
   // along grid x, whose extent is not limited to 65535
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(TPB, 1) k_sketch_fp32_simt(SimtParams p) {
 #pragma unroll
     for (int j = 0; j < T::TN / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  // generation task u (of 2) of the stage at l0 into buffer buf
+  // generation task u (of GT) of the stage at l0 into buffer buf
   auto gen = [&](float* buf, int64_t l0, int u) {
     if constexpr (LEFT)
       gen_task_fp32<T::BP, true>(buf, p, p0, p.P, l0, lend, u);
@@ -192,24 +202,24 @@ __global__ void __launch_bounds__(TPB, 1) k_sketch_fp32_simt(SimtParams p) {
 
   float4 pa[4];
   if (nst > 0) {
-    load_a<LEFT>(pa, p, p0, q0, lbeg, lend);
-    gen(smem_f, lbeg, 0);
-    gen(smem_f, lbeg, 1);
-    store_a<LEFT>(smem_f, pa);
+    load_a<LEFT, WIDE>(pa, p, p0, q0, lbeg, lend);
+#pragma unroll
+    for (int u = 0; u < T::GT; ++u) gen(smem_f, lbeg, u);
+    store_a<LEFT, WIDE>(smem_f, pa);
   }
   __syncthreads();
   for (int st = 0; st < nst; ++st) {
     const int64_t l0 = lbeg + static_cast<int64_t>(st) * BL;
     const bool more = st + 1 < nst;
     float* next = smem_f + ((st + 1) & 1) * T::STAGE;
-    if (more) load_a<LEFT>(pa, p, p0, q0, l0 + BL, lend);
+    if (more) load_a<LEFT, WIDE>(pa, p, p0, q0, l0 + BL, lend);
     const float* xs = smem_f + (st & 1) * T::STAGE;
     const float* ws = xs + BL * T::XW;
 #pragma unroll 2
     for (int l = 0; l < BL; ++l) {
       // the next stage's S tile is generated between this stage's FMAs (it
       // goes to the other buffer), so generation and FMAs share the cycles
-      if (more && (l == 2 || l == 9)) gen(next, l0 + BL, l == 2 ? 0 : 1);
+      if (more && l % (BL / T::GT) == 2) gen(next, l0 + BL, l / (BL / T::GT));
       float2 xr[T::TM];
       float2 wr[T::TN / 2];
 #pragma unroll
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(TPB, 1) k_sketch_fp32_simt(SimtParams p) {
 #pragma unroll
         for (int j = 0; j < T::TN / 2; ++j) acc[i][j] = __ffma2_rn(xr[i], wr[j], acc[i][j]);
     }
-    if (more) store_a<LEFT>(next, pa);
+    if (more) store_a<LEFT, WIDE>(next, pa);
     __syncthreads();
   }
 
@@ -303,18 +313,26 @@ __global__ void k_materialize(PhiloxKey key, int dist, int fmt, int scaled, floa
   }
 }
 
+// The left form takes the wide tile (128 x 256) when n is above 128, the
+// 256 x 128 tile otherwise (the right form always); both hold 32768 outputs.
+bool simt_wide(const GemmShape& s) { return s.left && s.Q > 128; }
+
 // The FP32 kernels' dynamic shared memory (two stage buffers: 64 / 80 KB)
 // is above the 48 KB default: allowed once per process.
 cudaError_t set_simt_smem() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_fp32_simt<true>,
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_fp32_simt<true, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(SimtTile<true>::SMEM));
+                                       static_cast<int>(SimtTile<true, true>::SMEM));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sketch_fp32_simt<false>,
+    e = cudaFuncSetAttribute(k_sketch_fp32_simt<true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(SimtTile<false>::SMEM));
+                             static_cast<int>(SimtTile<true, false>::SMEM));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sketch_fp32_simt<false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(SimtTile<false, false>::SMEM));
   done = e == cudaSuccess;
   return e;
 }
@@ -331,8 +349,9 @@ int num_sms() {
 }
 
 void plan_splits(const GemmShape& s, int* splits, int64_t* chunk) {
-  const int bp = s.left ? SimtTile<true>::BP : SimtTile<false>::BP;
-  const int bq = s.left ? SimtTile<true>::BQ : SimtTile<false>::BQ;
+  const bool wide = simt_wide(s);
+  const int bp = wide ? SimtTile<true, true>::BP : SimtTile<false, false>::BP;
+  const int bq = wide ? SimtTile<true, true>::BQ : SimtTile<false, false>::BQ;
   const int64_t tiles = ((s.P + bp - 1) / bp) * ((s.Q + bq - 1) / bq);
   const int64_t sms = num_sms();  // one CTA per SM (registers, shared memory)
   int64_t max_sp = s.L / (8 * BL) > 0 ? s.L / (8 * BL) : 1;
@@ -420,18 +439,22 @@ cudaError_t simt_sketch(const sk_sketch* h, const GemmShape& s, const float* A, 
     p.ldo = ldy;
   }
   // grid x: tiles of the long side (n or m); grid y: tiles of k, at most
-  // 65535 (k <= 8,388,480 in this form; a larger k fails the launch)
-  const int bp = s.left ? SimtTile<true>::BP : SimtTile<false>::BP;
-  const int bq = s.left ? SimtTile<true>::BQ : SimtTile<false>::BQ;
+  // 65535 (k <= 8,388,480 with the wide left tile, 16,776,960 with the
+  // 256-row ones; a larger k fails the launch)
+  const bool wide = simt_wide(s);
+  const int bp = wide ? SimtTile<true, true>::BP : SimtTile<false, false>::BP;
+  const int bq = wide ? SimtTile<true, true>::BQ : SimtTile<false, false>::BQ;
   const unsigned tq = (unsigned)((s.Q + bq - 1) / bq), tp = (unsigned)((s.P + bp - 1) / bp);
   dim3 grid(s.left ? tq : tp, s.left ? tp : tq, (unsigned)splits);
   cudaError_t e = set_simt_smem();
   if (e != cudaSuccess) return e;
   prof_mark(h->prof_start, st);
-  if (s.left)
-    k_sketch_fp32_simt<true><<<grid, TPB, SimtTile<true>::SMEM, st>>>(p);
+  if (s.left && wide)
+    k_sketch_fp32_simt<true, true><<<grid, TPB, SimtTile<true, true>::SMEM, st>>>(p);
+  else if (s.left)
+    k_sketch_fp32_simt<true, false><<<grid, TPB, SimtTile<true, false>::SMEM, st>>>(p);
   else
-    k_sketch_fp32_simt<false><<<grid, TPB, SimtTile<false>::SMEM, st>>>(p);
+    k_sketch_fp32_simt<false, false><<<grid, TPB, SimtTile<false, false>::SMEM, st>>>(p);
   prof_mark(h->prof_stop, st);
   count_launches(1);
   e = cudaGetLastError();

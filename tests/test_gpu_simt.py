@@ -176,10 +176,10 @@ def test_invalid_arguments(P):
 
 
 def test_right_fp32_beyond_65535_row_tiles(P, orc):
-    """A right sketch whose m needs more than 65535 tiles of 128 rows (the
+    """A right sketch whose m needs more than 65535 tiles of 256 rows (the
     long side runs along the launch grid's x extent): sampled rows of Y,
     including the last tile's, against the oracle."""
-    m, n, k, seed = 65536 * 128 + 300, 6, 24, 13
+    m, n, k, seed = 65536 * 256 + 300, 6, 24, 13
     A = torch.randn((m, n), generator=torch.Generator().manual_seed(seed))
     Y = torch.full((m, k), float("nan"), dtype=torch.float32, device="cuda")
     h = P.sk_create(seed, G, k)

@@ -78,12 +78,12 @@ def test_noalloc_cuda_error_is_reported_like_every_other_entry_point():
     """A CUDA failure inside the allocation-free call comes back as SK_ECUDA
     with sk_last_cuda_error describing it, as for the allocating call.  The
     failure used is one CUDA detects on the host before anything runs: in the
-    FP32 form a sketch size k above 65535 tiles of 128 rows is a launch grid
-    CUDA refuses."""
+    FP32 form a sketch size k above 65535 tiles of 256 rows (n <= 128) is a
+    launch grid CUDA refuses."""
     require_gpu()
     from paper_2603_20966_gb300 import _native as N
     L = N.lib()
-    k, m, n = 65536 * 128, 32, 4
+    k, m, n = 65536 * 256, 32, 4
     h = N.sk_create(3, N.SK_GAUSSIAN, k)
     try:
         A = torch.zeros((m, n), device="cuda")
