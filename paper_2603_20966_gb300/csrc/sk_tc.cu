@@ -892,29 +892,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // two TMEM accumulators (m rows 0-127 and 128-255 of its share), so one
 // generated S tile serves 512 rows of A.  Each CTA generates half of the
 // tile's k rows (the pair MMA splits N between the two CTAs).  Warp roles,
-// rings, chains and bounded waits are those of the left kernel.
+// chains and bounded waits are those of the left kernel.
+//
+// One ring of stages: the TMA brings a stage's FP32 A tile [256 rows][16]
+// into the slot, and the workers split it in place.  The 512 bytes of an
+// 8-row group of the FP32 tile become that group's K-major BF16 core
+// matrices, hi (256 bytes: 8 rows x 2 halves of 8 columns) then lo, so a warp
+// converts one group with no other warp involved, and the MMA reads hi and lo
+// with 512 bytes between 8-row groups.  With no separate staging ring the
+// slots are 20 KB and the ring is 11 stages deep, so up to 176 KB of A per
+// SM are in flight from HBM.
 // ---------------------------------------------------------------------------
 struct CfgR {
   static constexpr int ROWS = 256;  // rows of A per CTA (two 128-row accumulators)
   static constexpr int NGROUPS = 4;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NSF = 6;
-  static constexpr int NSO = 6;
-  static constexpr uint32_t STAGE_F = BK * ROWS * 4;  // FP32 staging [256 rows][16]
-  static constexpr uint32_t OPA = ROWS * BK * 2;      // hi or lo operand, 2 x 4 KB
+  static constexpr int NS = 11;                       // stages in the ring
+  static constexpr uint32_t OPA = BK * ROWS * 4;      // FP32 A tile = its hi and lo halves
+  static constexpr uint32_t ACC_A = OPA / 2;          // hi + lo of one 128-row accumulator
+  static constexpr uint32_t GROUP_A = 512;            // one 8-row group, FP32 = hi + lo
   static constexpr uint32_t OPS = 128 * BK * 2;       // this CTA's half of the S tile
-  static constexpr uint32_t OFF_F = 0;
-  static constexpr uint32_t OFF_AHI = OFF_F + NSF * STAGE_F;
-  static constexpr uint32_t OFF_ALO = OFF_AHI + NSO * OPA;
-  static constexpr uint32_t OFF_S = OFF_ALO + NSO * OPA;
-  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
-  // + per operand slot, the S rows received from the partner CTA
-  static constexpr uint32_t NUM_BARS = 2 * NSF + 3 * NSO + 3;
+  static constexpr uint32_t OFF_A = 0;
+  static constexpr uint32_t OFF_S = OFF_A + NS * OPA;
+  static constexpr uint32_t OFF_BAR = OFF_S + NS * OPS;
+  // per slot: A landed, operands ready, slot read by both pairs' MMAs, S rows
+  // received from the partner CTA; then the accumulator and drain barriers
+  static constexpr uint32_t NUM_BARS = 4 * NS + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
-  static_assert(NGROUPS <= NSF && NGROUPS <= NSO, "worker groups vs ring depth");
+  static_assert(NGROUPS <= NS, "worker groups vs ring depth");
+  static_assert(OPA % 1024 == 0 && OPS % 1024 == 0, "slots on 1 KB boundaries");
 };
 
 struct TcRightParams {
@@ -937,13 +946,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                              ~static_cast<uintptr_t>(1023));
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = sbase + C::OFF_BAR;
-  auto full_f = [&](int i) { return bar0 + 8u * i; };
-  auto empty_f = [&](int i) { return bar0 + 8u * (C::NSF + i); };
-  auto full_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + i); };
-  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSF + C::NSO + i); };
-  // s_recv: the S rows the partner CTA copies into operand slot i have landed
-  auto s_recv = [&](int i) { return bar0 + 8u * (2 * C::NSF + 2 * C::NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (2 * C::NSF + 3 * C::NSO);
+  // full_b: the slot's FP32 A tile has landed; full_o (even CTA): both CTAs'
+  // operands of the stage are ready; empty_o: both pairs' MMAs have read
+  // what this CTA wrote into the slot (here and, S rows, in its partner);
+  // s_recv: the S rows the partner CTA copies into the slot have landed
+  auto full_b = [&](int i) { return bar0 + 8u * i; };
+  auto full_o = [&](int i) { return bar0 + 8u * (C::NS + i); };
+  auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NS + i); };
+  auto s_recv = [&](int i) { return bar0 + 8u * (3 * C::NS + i); };
+  const uint32_t acc_full = bar0 + 8u * (4 * C::NS);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
@@ -975,11 +986,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nchains = (nsteps + CHAIN - 1) / CHAIN;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < C::NSF; ++i) {
-      mbar_init(full_f(i), 1);
-      mbar_init(empty_f(i), C::GROUP_WARPS);
-    }
-    for (int i = 0; i < C::NSO; ++i) {
+    for (int i = 0; i < C::NS; ++i) {
+      mbar_init(full_b(i), 1);
       mbar_init(full_o(i), C::GROUP_WARPS * 2);  // one worker group of each CTA of the pair
       mbar_init(empty_o(i), 2);  // the MMAs of both pairs read what this CTA wrote
       mbar_init(s_recv(i), 1);   // the receiving group's expect-tx, plus the copy's bytes
@@ -1011,43 +1019,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       int issued = 0;
       for (int s = 0; s < nsteps; ++s) {
-        const int sf = s % C::NSF;
-        if (s >= C::NSF && !mbar_wait(empty_f(sf), ((s / C::NSF) & 1) ^ 1, ab, 0x11, s)) break;
-        mbar_arrive_expect_tx(full_f(sf), C::STAGE_F);
-        tma_load_2d(sbase + C::OFF_F + sf * C::STAGE_F, &tmapA,
+        const int so = s % C::NS;
+        // both pairs' MMAs have read the slot's previous stage
+        if (s >= C::NS && !mbar_wait(empty_o(so), ((s / C::NS) & 1) ^ 1, ab, 0x13, s)) break;
+        mbar_arrive_expect_tx(full_b(so), C::OPA);
+        tma_load_2d(sbase + C::OFF_A + so * C::OPA, &tmapA,
                     static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK),
-                    static_cast<int32_t>(m0), full_f(sf));
+                    static_cast<int32_t>(m0), full_b(so));
         issued = s + 1;
       }
       if (*abort_flag) {
-        for (int s = max(0, issued - C::NSF); s < issued; ++s)
-          drain_wait(full_f(s % C::NSF), (s / C::NSF) & 1, 100000000ull);
+        for (int s = max(0, issued - C::NS); s < issued; ++s)
+          drain_wait(full_b(s % C::NS), (s / C::NS) & 1, 100000000ull);
       }
     }
   } else if (warp == WARP_MMA) {
     if (lane == 0 && leader) {
       const uint32_t idesc = idesc_bf16_f32(256u, static_cast<uint32_t>(nq));
+      // The single issuing thread's bookkeeping per stage bounds this kernel
+      // (it issues 4 MMAs per 512 tensor cycles), so the slot, phase and
+      // chain are counted, not divided, and every operand descriptor is a
+      // base descriptor plus offset / 16 in its low word (exact: all offsets
+      // are multiples of 16 B and every operand lies below 256 KB).
+      const uint64_t a_base = smem_desc(sbase + C::OFF_A, LBO, C::GROUP_A);
+      const uint64_t b_base = smem_desc(sbase + C::OFF_S, LBO, SBO);
+      const uint32_t a_lo = static_cast<uint32_t>(a_base);
+      const uint64_t a_hi = a_base & 0xFFFFFFFF00000000ull;
+      const uint32_t b_lo = static_cast<uint32_t>(b_base);
+      const uint64_t b_hi = b_base & 0xFFFFFFFF00000000ull;
+      int so = 0, in_chain = 0, chain_no = 0;
+      uint32_t ph = 0;
       for (int s = 0; s < nsteps; ++s) {
-        const int so = s % C::NSO;
-        const int in_chain = s % CHAIN;
-        if (s > 0 && in_chain == 0 &&
-            !mbar_wait(acc_empty, ((s / CHAIN) - 1) & 1, ab, 0x25, s))
+        const bool chain_start = s == 0 || in_chain == 0;
+        if (s > 0 && in_chain == 0 && !mbar_wait(acc_empty, (chain_no - 1) & 1, ab, 0x25, s))
           break;
-        if (!mbar_wait(full_o(so), (s / C::NSO) & 1, ab, 0x22, s)) break;
+        if (!mbar_wait(full_o(so), ph, ab, 0x22, s)) break;
         tc_fence_after();
-        const uint64_t bdesc = smem_desc(sbase + C::OFF_S + so * C::OPS, LBO, SBO);
+        const uint32_t a_slot = a_lo + static_cast<uint32_t>(so) * (C::OPA >> 4);
+        const uint64_t bdesc = b_hi | (b_lo + static_cast<uint32_t>(so) * (C::OPS >> 4));
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
-          const uint32_t ab_ = sbase + (pass ? C::OFF_ALO : C::OFF_AHI) + so * C::OPA;
+          // hi (pass 0) or lo (pass 1) of accumulator j: 8-row groups 512 B apart
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            const uint64_t adesc = smem_desc(ab_ + static_cast<uint32_t>(j) * (C::OPA / 2), LBO, SBO);
+            const uint64_t adesc =
+                a_hi | (a_slot + ((static_cast<uint32_t>(pass) * 256u +
+                                   static_cast<uint32_t>(j) * C::ACC_A) >> 4));
             mma_bf16_pair(tmem + static_cast<uint32_t>(j * nq), adesc, bdesc, idesc,
-                          (in_chain > 0 || pass > 0) ? 1u : 0u);
+                          (!chain_start || pass > 0) ? 1u : 0u);
           }
         }
         mma_commit_pair_mask(empty_o(so), 0xF);  // all four CTAs wrote into the slot
         if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit_pair_mask(acc_full, pair_mask);
+        if (++in_chain == CHAIN) {
+          in_chain = 0;
+          ++chain_no;
+        }
+        if (++so == C::NS) {
+          so = 0;
+          ph ^= 1u;
+        }
       }
       mma_commit_pair(drain_bar);
       drain_wait(drain_bar, 0, 200000000ull);
@@ -1122,11 +1153,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint4 words = make_uint4(0u, 0u, 0u, 0u);
     int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
     for (int s = grp; s < nsteps; s += C::NGROUPS) {
-      const int sf = s % C::NSF;
-      const int so = s % C::NSO;
+      const int so = s % C::NS;
       // both pairs' MMAs have read what this CTA wrote into slot `so` (here
       // and in its partner) last time
-      bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
+      bool ok = s < C::NS || mbar_wait(empty_o(so), ((s / C::NS) & 1) ^ 1, ab, 0x43, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
       // the partner's half of this CTA's S rows will land here
@@ -1191,57 +1221,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0 && w_bytes != 0)
         bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + w_off,
                              smem_u32(sdst) + w_off, w_bytes, partner_s_recv + 8u * so);
-      ok = mbar_wait(full_f(sf), (s / C::NSF) & 1, ab, 0x40, s);
+      ok = mbar_wait(full_b(so), (s / C::NS) & 1, ab, 0x40, s);
       if (!__all_sync(0xffffffffu, ok)) break;
-      const float* stg = reinterpret_cast<const float*>(smem + C::OFF_F + sf * C::STAGE_F);
-      uint8_t* ahi = smem + C::OFF_AHI + so * C::OPA;
-      uint8_t* alo = smem + C::OFF_ALO + so * C::OPA;
-      constexpr int CONV_IT = (2 * C::ROWS + C::GROUP_THREADS - 1) / C::GROUP_THREADS;
-#pragma unroll
-      for (int it = 0; it < CONV_IT; ++it) {
-        // task i: row (0..255: accumulator row / 128, lane row % 128) and
-        // 8-column half hh.  The 8 lanes of a 16-byte access phase take 8
-        // consecutive rows, so their operand stores fall in 8 different
-        // 16-byte units (no conflict), with the halves alternating so that
-        // their staging reads (64-byte rows) spread over 4 bank groups.
-        const int i = wt + it * C::GROUP_THREADS;
-        const int l = i & 7;
-        const int blk = i >> 3;
-        const int row = 8 * (blk >> 1) + l;
-        const int hh = ((l >> 1) & 1) ^ (blk & 1);
-        const float4 x0 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh);
-        const float4 x1 = *reinterpret_cast<const float4*>(stg + row * BK + 8 * hh + 4);
-        const float a[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hw[e] = pack_bf16x2(a[2 * e], a[2 * e + 1]);
-          const float2 hv = f2(__uint_as_float(hw[e] << 16), __uint_as_float(hw[e] & 0xffff0000u));
+      // split the FP32 A tile in place, one 8-row group (512 bytes) per warp
+      // at a time: lane = (row r = lane / 4, columns 4 (lane % 4) ..); the
+      // group's hi core matrices (columns 0-7, then 8-15; 8 rows x 16 bytes)
+      // replace its first 256 bytes, lo its last 256
+      {
+        uint8_t* slot = smem + C::OFF_A + so * C::OPA;
+        const uint32_t r = static_cast<uint32_t>(lane) >> 2;
+        const uint32_t c4 = static_cast<uint32_t>(lane) & 3u;
+        const uint32_t dst = (c4 >> 1) * 128u + r * 16u + (c4 & 1u) * 8u;
+#pragma unroll 2
+        for (int gi = wg; gi < C::ROWS / 8; gi += C::GROUP_WARPS) {
+          uint8_t* grp8 = slot + gi * C::GROUP_A;
+          const float4 x = *reinterpret_cast<const float4*>(grp8 + r * 64u + c4 * 16u);
+          __syncwarp();  // the warp's group has been read
+          const uint32_t h0 = pack_bf16x2(x.x, x.y), h1 = pack_bf16x2(x.z, x.w);
           // a - hi of both elements in one packed FMA (the product by -1 is
           // exact, so each component is the rounded difference)
-          const float2 lv = __ffma2_rn(hv, f2(-1.0f, -1.0f), f2(a[2 * e], a[2 * e + 1]));
-          lw[e] = pack_bf16x2(lv.x, lv.y);
+          const float2 l0 = __ffma2_rn(f2(__uint_as_float(h0 << 16), __uint_as_float(h0 & 0xffff0000u)),
+                                       f2(-1.0f, -1.0f), f2(x.x, x.y));
+          const float2 l1 = __ffma2_rn(f2(__uint_as_float(h1 << 16), __uint_as_float(h1 & 0xffff0000u)),
+                                       f2(-1.0f, -1.0f), f2(x.z, x.w));
+          *reinterpret_cast<uint2*>(grp8 + dst) = make_uint2(h0, h1);
+          *reinterpret_cast<uint2*>(grp8 + 256u + dst) =
+              make_uint2(pack_bf16x2(l0.x, l0.y), pack_bf16x2(l1.x, l1.y));
         }
-        const uint32_t o = static_cast<uint32_t>(row >> 7) * (C::OPA / 2) +
-                           kmaj_off(static_cast<uint32_t>(row & 127), static_cast<uint32_t>(hh));
-        *reinterpret_cast<uint4*>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       // the S half and the A operands are in this CTA's own shared memory;
       // the group's first warp certifies the partner's rows too
       fence_proxy_async_smem();
-      ok = !gfirst || mbar_wait(s_recv(so), (s / C::NSO) & 1, ab, 0x46, s);
+      ok = !gfirst || mbar_wait(s_recv(so), (s / C::NS) & 1, ab, 0x46, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       pend = -1;
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive_cluster(lead_full_o + 8u * so);
-        mbar_arrive(empty_f(sf));
-      }
+      if (lane == 0) mbar_arrive_cluster(lead_full_o + 8u * so);
     }
     // leaving early: let a copy the partner may still be sending land first
     if (gfirst && pend >= 0 && lane == 0)
-      drain_wait(s_recv(pend % C::NSO), (pend / C::NSO) & 1, 100000000ull);
+      drain_wait(s_recv(pend % C::NS), (pend / C::NS) & 1, 100000000ull);
   }
 
   tc_fence_before();
