@@ -1319,7 +1319,8 @@ struct CfgQ {
   static constexpr uint32_t OPS = 128 * QK;   // 16 KB: this CTA's half of the S tile
   static constexpr uint32_t OFF_A = 0;
   static constexpr uint32_t OFF_S = OFF_A + NSO * OPA;
-  static constexpr uint32_t OFF_BAR = OFF_S + NSO * OPS;
+  static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;  // epilogue transpose tiles
+  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
   static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
@@ -1466,10 +1467,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp < WARP_WORK0) {
     // ---- epilogue: accumulator j holds rows m0 + 128 j + lane, columns q0 + c ----
+    // Each row is scaled by its 2^e as it is read from TMEM, then written
+    // through a per-warp transpose tile in 64-byte pieces of 8 rows (as in
+    // the BF16 right sketch).
     const int quarter = warp & 3;
     const int colset = (warp - WARP_EPI0) >> 2;
     const bool vec_ok = (p.Q % 4) == 0;
     const int nchunk = (nq + 31) / 32;
+    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * EPI_TILE);
+    const int rsub = lane >> 2;       // row within a group of 8 (read side)
+    const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
     for (int c0 = 0; c0 < nchains; ++c0) {
       const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -1482,37 +1489,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       static_cast<uint32_t>(j * nq + ci * 32),
                   v);
         tmem_ld_wait();
-        const int64_t gm = m0 + j * 128 + quarter * 32 + lane;
-        if (gm < p.P) {
-          const int e = p.exps[gm];  // the row's scale 2^e: an exact multiply
-          float* drow = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + q0;
+        const int64_t grow0 = m0 + j * 128 + quarter * 32;  // the warp's first row of m
+        const int64_t gl = grow0 + lane;                     // this lane's row (write side)
+        const int e = gl < p.P ? p.exps[gl] : 0;  // the row's scale 2^e: an exact multiply
 #pragma unroll
-          for (int u4 = 0; u4 < 32; u4 += 4) {
-            const int c = ci * 32 + u4;
-            if (c >= nq) continue;
-            const int64_t col = q0 + c;
-            const float a0 = ldexpf(__uint_as_float(v[u4]), e);
-            const float a1 = ldexpf(__uint_as_float(v[u4 + 1]), e);
-            const float a2 = ldexpf(__uint_as_float(v[u4 + 2]), e);
-            const float a3 = ldexpf(__uint_as_float(v[u4 + 3]), e);
-            float* d = drow + c;
-            if (vec_ok && col + 4 <= p.Q) {
-              if (c0 == 0)
-                *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
-              else
-                red_add_v4(d, a0, a1, a2, a3);
-            } else {
-              const float vv[4] = {a0, a1, a2, a3};
-              for (int u = 0; u < 4; ++u) {
-                if (col + u < p.Q) {
-                  if (c0 == 0)
-                    d[u] = vv[u];
-                  else
-                    red_add(d + u, vv[u]);
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
+                make_float4(ldexpf(__uint_as_float(v[16 * half + 4 * q]), e),
+                            ldexpf(__uint_as_float(v[16 * half + 4 * q + 1]), e),
+                            ldexpf(__uint_as_float(v[16 * half + 4 * q + 2]), e),
+                            ldexpf(__uint_as_float(v[16 * half + 4 * q + 3]), e));
+          __syncwarp();
+          const int c = ci * 32 + 16 * half + csub;
+          const int64_t col = q0 + c;
+#pragma unroll
+          for (int pass = 0; pass < 4; ++pass) {
+            const int rr = 8 * pass + rsub;
+            const int64_t gm = grow0 + rr;
+            const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
+            if (gm < p.P && c < nq) {
+              float* d = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + col;
+              if (vec_ok && col + 4 <= p.Q) {
+                if (c0 == 0)
+                  *reinterpret_cast<float4*>(d) = a;
+                else
+                  red_add_v4(d, a.x, a.y, a.z, a.w);
+              } else {
+                const float vv[4] = {a.x, a.y, a.z, a.w};
+                for (int u = 0; u < 4; ++u) {
+                  if (col + u < p.Q && c + u < nq) {
+                    if (c0 == 0)
+                      d[u] = vv[u];
+                    else
+                      red_add(d + u, vv[u]);
+                  }
                 }
               }
             }
           }
+          __syncwarp();
         }
       }
       tc_fence_before();
