@@ -900,23 +900,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // matrices, hi (256 bytes: 8 rows x 2 halves of 8 columns) then lo, so a warp
 // converts one group with no other warp involved, and the MMA reads hi and lo
 // with 512 bytes between 8-row groups.  With no separate staging ring the
-// slots are 20 KB and the ring is 10 stages deep, so up to 160 KB of A per
-// SM are in flight from HBM.
+// slots are 20 KB and the ring is 9 stages deep, so up to 144 KB of A per SM
+// are in flight from HBM.
 // ---------------------------------------------------------------------------
 struct CfgR {
   static constexpr int ROWS = 256;  // rows of A per CTA (two 128-row accumulators)
   static constexpr int NGROUPS = 4;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NS = 10;                       // stages in the ring
+  static constexpr int NS = 9;                        // stages in the ring
   static constexpr uint32_t OPA = BK * ROWS * 4;      // FP32 A tile = its hi and lo halves
   static constexpr uint32_t ACC_A = OPA / 2;          // hi + lo of one 128-row accumulator
   static constexpr uint32_t GROUP_A = 512;            // one 8-row group, FP32 = hi + lo
   static constexpr uint32_t OPS = 128 * BK * 2;       // this CTA's half of the S tile
   static constexpr uint32_t OFF_A = 0;
   static constexpr uint32_t OFF_S = OFF_A + NS * OPA;
-  static constexpr uint32_t OFF_EPI = OFF_S + NS * OPS;  // epilogue transpose tiles
-  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
+  // epilogue transpose tiles: 32 rows x 32 columns (pitch 36 floats) per warp
+  static constexpr int EPI_PITCH_R = 36;
+  static constexpr uint32_t EPI_TILE_R = 32 * EPI_PITCH_R * 4;
+  static constexpr uint32_t OFF_EPI = OFF_S + NS * OPS;
+  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE_R;
   // per slot: A landed, operands ready, slot read by both pairs' MMAs, S rows
   // received from the partner CTA; then the accumulator and drain barriers
   static constexpr uint32_t NUM_BARS = 4 * NS + 3;
@@ -1088,16 +1091,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- epilogue: accumulator j holds rows m0 + 128 j + lane, columns q0 + c ----
     // A warp reads 32 accumulator rows (its TMEM lane quarter) x 32 columns
     // and writes them through a transpose tile, so that every global store /
-    // reduction instruction covers 64-byte pieces of 8 rows instead of 16
-    // bytes of 32 rows (a quarter of the memory requests: the drain of a
+    // reduction instruction covers whole 128-byte rows, 4 of them, instead of
+    // 16 bytes of 32 rows (an eighth of the memory requests: the drain of a
     // chain stalls the MMA issuer, which waits for the whole TMEM).
     const int quarter = warp & 3;
     const int colset = (warp - WARP_EPI0) >> 2;
     const bool vec_ok = (p.Q % 4) == 0;
     const int nchunk = (nq + 31) / 32;
-    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * EPI_TILE);
-    const int rsub = lane >> 2;       // row within a group of 8 (read side)
-    const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
+    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_TILE_R);
+    const int rsub = lane >> 3;       // row within a group of 4 (read side)
+    const int csub = (lane & 7) * 4;  // first of 4 columns (read side)
     for (int c0 = 0; c0 < nchains; ++c0) {
       const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -1111,46 +1114,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   v);
         tmem_ld_wait();
         const int64_t grow0 = m0 + j * 128 + quarter * 32;  // the warp's first row of m
+        // lane = accumulator row: its 32 columns into the tile
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          // lane = accumulator row: its 16 columns into the tile
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(tile + lane * C::EPI_PITCH_R + 4 * q) =
+              make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        __syncwarp();
+        const int c = ci * 32 + csub;  // column of the pair's k rows
+        const int64_t col = q0 + c;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
-                make_float4(__uint_as_float(v[16 * half + 4 * q]),
-                            __uint_as_float(v[16 * half + 4 * q + 1]),
-                            __uint_as_float(v[16 * half + 4 * q + 2]),
-                            __uint_as_float(v[16 * half + 4 * q + 3]));
-          __syncwarp();
-          const int c = ci * 32 + 16 * half + csub;  // column of the pair's k rows
-          const int64_t col = q0 + c;
-#pragma unroll
-          for (int pass = 0; pass < 4; ++pass) {
-            const int rr = 8 * pass + rsub;
-            const int64_t gm = grow0 + rr;
-            const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
-            if (gm < p.P && c < nq) {
-              float* d = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + col;
-              if (vec_ok && col + 4 <= p.Q) {
-                if (c0 == 0)
-                  *reinterpret_cast<float4*>(d) = a;
-                else
-                  red_add_v4(d, a.x, a.y, a.z, a.w);
-              } else {
-                const float vv[4] = {a.x, a.y, a.z, a.w};
-                for (int u = 0; u < 4; ++u) {
-                  if (col + u < p.Q && c + u < nq) {
-                    if (c0 == 0)
-                      d[u] = vv[u];
-                    else
-                      red_add(d + u, vv[u]);
-                  }
+        for (int pass = 0; pass < 8; ++pass) {
+          const int rr = 4 * pass + rsub;
+          const int64_t gm = grow0 + rr;
+          const float4 a = *reinterpret_cast<const float4*>(tile + rr * C::EPI_PITCH_R + csub);
+          if (gm < p.P && c < nq) {
+            float* d = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + col;
+            if (vec_ok && col + 4 <= p.Q) {
+              if (c0 == 0)
+                *reinterpret_cast<float4*>(d) = a;
+              else
+                red_add_v4(d, a.x, a.y, a.z, a.w);
+            } else {
+              const float vv[4] = {a.x, a.y, a.z, a.w};
+              for (int u = 0; u < 4; ++u) {
+                if (col + u < p.Q && c + u < nq) {
+                  if (c0 == 0)
+                    d[u] = vv[u];
+                  else
+                    red_add(d + u, vv[u]);
                 }
               }
             }
           }
-          __syncwarp();
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
