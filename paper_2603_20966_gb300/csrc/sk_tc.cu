@@ -156,8 +156,9 @@ struct alignas(128) LeftProblem {
   // 128-byte swizzle (`amap`: one 3D box of all the CTA's blocks when n is a
   // multiple of 32 (1), else one 2D box per block (2)) and the workers split
   // it into the BF16 halves in
-  // place (single Rademacher sketches; see convert_stage); 0: the split pass
-  // wrote the halves and `map` loads them
+  // place (single sketches on pairs and the Rademacher members of batches;
+  // see convert_stage); 0: the split pass wrote the halves and `map` loads
+  // them
   int conv_inline;
   CUtensorMap amap;
 };
@@ -343,14 +344,15 @@ __device__ __forceinline__ ItemGeo item_geo(const LeftSched& sc, int idx, uint32
 // each 128-byte phase of a 16-byte access then read (and write) one unit of
 // each of 8 rows, and the swizzle puts those 8 units in 8 different bank
 // groups, so no access of the conversion has a bank conflict.
-template <class C>
-__device__ __forceinline__ void convert_stage(uint8_t* slot, int cols, int wt) {
-  static_assert(C::GROUP_THREADS == 128, "4 threads per row of a 32-row stage");
+// wt is the thread's index in a set of 4 warps (128 threads, 4 threads per
+// row of the 32-row stage); the set converts chunks c0, c0 + cstep, ...
+__device__ __forceinline__ void convert_stage(uint8_t* slot, int cols, int wt, int c0 = 0,
+                                              int cstep = 1) {
   const uint32_t r = (static_cast<uint32_t>(wt) >> 5) * 8u + (static_cast<uint32_t>(wt) & 7u);
   const uint32_t j = (static_cast<uint32_t>(wt) >> 3) & 3u;  // 16-column quarter of the chunk
   const uint32_t sw = r & 7u;
   const uint32_t u0 = ((2u * j) ^ sw) * 16u, u1 = ((2u * j + 1u) ^ sw) * 16u;
-  for (int c = 0; c < cols / HCHUNK; ++c) {
+  for (int c = c0; c < cols / HCHUNK; c += cstep) {
     uint8_t* ch = slot + c * (2 * HCHUNK_BYTES);
     const uint8_t* src = ch + (j >> 1) * HCHUNK_BYTES + r * 128u;
     float a[16];
@@ -469,6 +471,85 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, const
   }
 }
 
+// One accumulator drain by an epilogue warp of the left kernel (the steps of
+// the kernel's own epilogue loop): wait until chain gc has finished, read the
+// warp's TMEM lane quarter x its 32-column chunks, write them through the
+// transpose tile into the item's partial (first chain: store; later: add),
+// and release the accumulator.  Out of line for the epilogue warps that also
+// split A (EC), so that their stage loop does not hold the drain's registers.
+template <bool PAIR>
+__device__ __noinline__ bool drain_chain_left(uint32_t tmem, int quarter, int colset, float* tile,
+                                              const ItemGeo ig, float* part_item, bool first,
+                                              uint32_t acc_full, uint32_t lead_acc_empty, int gc,
+                                              const Abort ab) {
+  const int lane = threadIdx.x & 31;
+  const int rsub = lane >> 2;       // row within a group of 8 (read side)
+  const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
+  const int64_t P = ig.pr->P, Q = ig.pr->Q;
+  const bool vec_ok = (Q % 4) == 0;
+  const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
+  if (!__all_sync(0xffffffffu, ok)) return false;  // tcgen05.ld below is warp-collective
+  tc_fence_after();
+  for (int ci = colset; ci * 32 < (ig.nmma - 1) * 256 + ig.nh; ci += 2) {
+    uint32_t v[32];
+    tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(ci * 32),
+              v);
+    tmem_ld_wait();
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
+            make_float4(__uint_as_float(v[16 * half + 4 * q]),
+                        __uint_as_float(v[16 * half + 4 * q + 1]),
+                        __uint_as_float(v[16 * half + 4 * q + 2]),
+                        __uint_as_float(v[16 * half + 4 * q + 3]));
+      __syncwarp();
+      const int tcol = ci * 32 + 16 * half + csub;
+      const int h = tcol >> 8;
+      const int c = tcol & 255;
+      const int tn =
+          PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh)) : tcol;
+      const int64_t col = ig.q0 + tn;
+#pragma unroll
+      for (int pass = 0; pass < 4; ++pass) {
+        const int rr = 8 * pass + rsub;
+        const int64_t gp = ig.p0 + quarter * 32 + rr;
+        const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
+        if (c < ig.nh && gp < P) {
+          float* d = part_item + gp * Q + tn;
+          if (vec_ok && col + 4 <= Q) {
+            if (first)
+              *reinterpret_cast<float4*>(d) = a;
+            else
+              red_add_v4(d, a.x, a.y, a.z, a.w);
+          } else {
+            const float vv[4] = {a.x, a.y, a.z, a.w};
+            for (int u = 0; u < 4; ++u) {
+              if (col + u < Q) {
+                if (first)
+                  d[u] = vv[u];
+                else
+                  red_add(d + u, vv[u]);
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) {
+    if (PAIR)
+      mbar_arrive_cluster(lead_acc_empty);
+    else
+      mbar_arrive(lead_acc_empty);
+  }
+  return true;
+}
+
 // Persistent left-sketch kernel: each pair (or single CTA) runs its list of
 // items back to back; ring positions, barrier phases and accumulation chains
 // are counted across items (g = stage counter, gc = chain counter).  DIST is
@@ -479,10 +560,15 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, const
 constexpr int kMixed = -1;
 constexpr int kStored = 3;
 
-template <int DIST, bool PAIR, bool NARROW = false>
+template <int DIST, bool PAIR, bool NARROW = false, bool ECONV = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_sketch_bf16x2_left(const LeftSched sc) {
   using C = Cfg<PAIR, NARROW>;
+  // EC (pairs): the epilogue warps certify every stage's A tile to the MMA
+  // issuer, and split in place the FP32 tiles of Gaussian and uniform items
+  // (their workers are busy generating; the epilogue warps are idle between
+  // accumulator drains), so no split pass runs before those items
+  constexpr bool EC = ECONV && PAIR;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -513,7 +599,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NSO; ++i) {
       mbar_init(full_b(i), 1);
-      mbar_init(full_o(i), C::GROUP_WARPS * (PAIR ? 2 : 1));  // one worker group of each CTA
+      // one worker group of each CTA (plus, with EC, the epilogue warps of each)
+      mbar_init(full_o(i), (C::GROUP_WARPS + (EC ? NUM_EPI_WARPS : 0)) * (PAIR ? 2 : 1));
       mbar_init(empty_o(i), 1);
     }
     mbar_init(acc_full, 1);
@@ -593,8 +680,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             (DIST == kStored ? C::OPS : 0u);               // + the S tile
         const int32_t z0 =
             static_cast<int32_t>((ig.q0 + static_cast<int64_t>(rank) * ig.cols) / HCHUNK);
-        // FP32 A, split in place by the workers (Rademacher items on pairs)
-        const bool conv = (DIST == kRademacher || DIST == kMixed) && PAIR && ig.pr->conv_inline;
+        // FP32 A, split in place by the workers (Rademacher items on pairs) or
+        // by the epilogue warps (EC)
+        const bool conv =
+            (DIST == kRademacher || DIST == kMixed || EC) && PAIR && ig.pr->conv_inline;
         const int32_t x0 = static_cast<int32_t>(ig.q0 + static_cast<int64_t>(rank) * ig.cols);
         if (conv) tma_prefetch_desc(&ig.pr->amap);
         for (int s = 0; s < ig.nsteps; ++s, ++g) {
@@ -637,7 +726,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             idesc_bf16_f32(PAIR ? 256u : 128u, static_cast<uint32_t>(ig.nh)) | IDESC_B_MN_MAJOR;
         // split A as loaded: [hi chunks][lo chunks] of 64 columns (4 KB each),
         // or, converted in place, [chunk][hi, lo] (8 KB per chunk)
-        const bool inl = (DIST == kRademacher || DIST == kMixed) && PAIR && ig.pr->conv_inline;
+        const bool inl =
+            (DIST == kRademacher || DIST == kMixed || EC) && PAIR && ig.pr->conv_inline;
         const uint32_t chunk_stride = inl ? 2 * HCHUNK_BYTES : HCHUNK_BYTES;
         const uint32_t pstride =
             inl ? HCHUNK_BYTES : static_cast<uint32_t>(ig.cols * LK * 2);  // hi -> lo tile
@@ -717,86 +807,140 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * EPI_TILE);
     const int rsub = lane >> 2;       // row within a group of 8 (read side)
     const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
-    int gc = 0;
-    bool stop = false;
-    for (int j = 0; !stop; ++j) {
-      const int idx = read_item_warp(j);
-      if (idx < 0) break;
-      const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
-      const LeftItem it = sc.items[idx];
-      const int64_t P = ig.pr->P, Q = ig.pr->Q;
-      float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * Q + ig.q0;
-      const bool vec_ok = (Q % 4) == 0;
-      const int nchains = (ig.nsteps + ig.coff + ig.chain - 1) / ig.chain;
-      for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
-        const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
-        if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
-          stop = true;
-          break;
+    if constexpr (EC) {
+      // Split each stage's FP32 A tile in place (4-warp sets take alternate
+      // 64-column chunks) and certify it to the MMA issuer; the chain that
+      // ended at a stage is drained once the next stage is certified, so
+      // the MMA issuer finds an operand ready when the accumulator frees.
+      const int ew = warp - WARP_EPI0;
+      const int cwt = (ew & 3) * 32 + lane;  // thread index in its 4-warp set
+      const int cset = ew >> 2;
+      int g = 0, gc = 0;
+      bool stop = false;
+      int pend = -1;  // item whose chain ended at the last certified stage, or -1
+      bool pend_first = false;
+      auto drain_pending = [&]() -> bool {
+        const ItemGeo pg = item_geo<PAIR>(sc, pend, rank);
+        const LeftItem it = sc.items[pend];
+        float* part_item = pg.pr->part + static_cast<int64_t>(it.z) * pg.pr->P * pg.pr->Q + pg.q0;
+        return drain_chain_left<PAIR>(tmem, quarter, colset, tile, pg, part_item, pend_first,
+                                      acc_full, lead_acc_empty, gc++, ab);
+      };
+      for (int j = 0; !stop; ++j) {
+        const int idx = read_item_warp(j);
+        if (idx < 0) break;
+        const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
+        int chains = 0;  // chains of this item begun so far
+        for (int s = 0; s < ig.nsteps; ++s, ++g) {
+          const int so = g % C::NSO;
+          const bool ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x30, g);
+          if (!__all_sync(0xffffffffu, ok)) {
+            stop = true;
+            break;
+          }
+          if (ig.pr->conv_inline && (DIST == kMixed ? ig.dist : DIST) != kRademacher)
+            convert_stage(smem + C::OFF_B + so * C::OPB, ig.cols, cwt, cset, 2);
+          fence_proxy_async_smem();  // the split tile is read by the tensor core
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(lead_full_o + 8u * so);
+          if (pend >= 0) {
+            if (!drain_pending()) {
+              stop = true;
+              break;
+            }
+            pend = -1;
+          }
+          const int ph = (s + ig.coff) & (ig.chain - 1);
+          if (ph == ig.chain - 1 || s == ig.nsteps - 1) {  // a chain ends at this stage
+            pend = idx;
+            pend_first = chains == 0;
+            ++chains;
+          }
         }
-        tc_fence_after();
-        // TMEM column h*256 + c holds B row c of instruction h: with a pair,
-        // rows c < bh are the even CTA's columns h*bh + c of the tile and rows
-        // c >= bh the odd CTA's columns cols + h*bh + (c - bh)
-        for (int ci = colset; ci * 32 < (ig.nmma - 1) * 256 + ig.nh; ci += 2) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                        static_cast<uint32_t>(ci * 32),
-                    v);
-          tmem_ld_wait();
-#pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            // lane = accumulator row: its 16 columns into the tile
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
-                  make_float4(__uint_as_float(v[16 * half + 4 * q]),
-                              __uint_as_float(v[16 * half + 4 * q + 1]),
-                              __uint_as_float(v[16 * half + 4 * q + 2]),
-                              __uint_as_float(v[16 * half + 4 * q + 3]));
-            __syncwarp();
-            // 4 consecutive columns (bh is a multiple of 8: they never straddle)
-            const int tcol = ci * 32 + 16 * half + csub;
-            const int h = tcol >> 8;
-            const int c = tcol & 255;
-            const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
-                                : tcol;
-            const int64_t col = ig.q0 + tn;
-#pragma unroll
-            for (int pass = 0; pass < 4; ++pass) {
-              const int rr = 8 * pass + rsub;
-              const int64_t gp = ig.p0 + quarter * 32 + rr;
-              const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
-              if (c < ig.nh && gp < P) {
-                float* d = part_item + gp * Q + tn;
-                if (vec_ok && col + 4 <= Q) {
-                  if (c0 == 0)
-                    *reinterpret_cast<float4*>(d) = a;
-                  else
-                    red_add_v4(d, a.x, a.y, a.z, a.w);
-                } else {
-                  const float vv[4] = {a.x, a.y, a.z, a.w};
-                  for (int u = 0; u < 4; ++u) {
-                    if (col + u < Q) {
-                      if (c0 == 0)
-                        d[u] = vv[u];
-                      else
-                        red_add(d + u, vv[u]);
+      }
+      if (pend >= 0 && !stop) drain_pending();
+    } else {
+      int gc = 0;
+      bool stop = false;
+      for (int j = 0; !stop; ++j) {
+        const int idx = read_item_warp(j);
+        if (idx < 0) break;
+        const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
+        const LeftItem it = sc.items[idx];
+        const int64_t P = ig.pr->P, Q = ig.pr->Q;
+        float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * Q + ig.q0;
+        const bool vec_ok = (Q % 4) == 0;
+        const int nchains = (ig.nsteps + ig.coff + ig.chain - 1) / ig.chain;
+        for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
+          const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
+          if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          // TMEM column h*256 + c holds B row c of instruction h: with a pair,
+          // rows c < bh are the even CTA's columns h*bh + c of the tile and rows
+          // c >= bh the odd CTA's columns cols + h*bh + (c - bh)
+          for (int ci = colset; ci * 32 < (ig.nmma - 1) * 256 + ig.nh; ci += 2) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                          static_cast<uint32_t>(ci * 32),
+                      v);
+            tmem_ld_wait();
+  #pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              // lane = accumulator row: its 16 columns into the tile
+  #pragma unroll
+              for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
+                    make_float4(__uint_as_float(v[16 * half + 4 * q]),
+                                __uint_as_float(v[16 * half + 4 * q + 1]),
+                                __uint_as_float(v[16 * half + 4 * q + 2]),
+                                __uint_as_float(v[16 * half + 4 * q + 3]));
+              __syncwarp();
+              // 4 consecutive columns (bh is a multiple of 8: they never straddle)
+              const int tcol = ci * 32 + 16 * half + csub;
+              const int h = tcol >> 8;
+              const int c = tcol & 255;
+              const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
+                                  : tcol;
+              const int64_t col = ig.q0 + tn;
+  #pragma unroll
+              for (int pass = 0; pass < 4; ++pass) {
+                const int rr = 8 * pass + rsub;
+                const int64_t gp = ig.p0 + quarter * 32 + rr;
+                const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
+                if (c < ig.nh && gp < P) {
+                  float* d = part_item + gp * Q + tn;
+                  if (vec_ok && col + 4 <= Q) {
+                    if (c0 == 0)
+                      *reinterpret_cast<float4*>(d) = a;
+                    else
+                      red_add_v4(d, a.x, a.y, a.z, a.w);
+                  } else {
+                    const float vv[4] = {a.x, a.y, a.z, a.w};
+                    for (int u = 0; u < 4; ++u) {
+                      if (col + u < Q) {
+                        if (c0 == 0)
+                          d[u] = vv[u];
+                        else
+                          red_add(d + u, vv[u]);
+                      }
                     }
                   }
                 }
               }
+              __syncwarp();
             }
-            __syncwarp();
           }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (PAIR)
-            mbar_arrive_cluster(lead_acc_empty);
-          else
-            mbar_arrive(acc_empty);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if (PAIR)
+              mbar_arrive_cluster(lead_acc_empty);
+            else
+              mbar_arrive(acc_empty);
+          }
         }
       }
     }
@@ -846,16 +990,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           else
             gen_stage<kGaussian, C>(sdst, ig, ig.key, cbase, wt, cached_blk, words);
         }
-        // this CTA's split A tile of the stage has landed
-        ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x40, g);
-        if (!__all_sync(0xffffffffu, ok)) {
-          stop = true;
-          break;
+        // FP32 A of a Rademacher item: the workers split it (the sign bits
+        // leave them idle)
+        const bool wconv = (DIST == kRademacher || DIST == kMixed) && PAIR &&
+                           ig.pr->conv_inline && (DIST != kMixed || ig.dist == kRademacher);
+        if (!EC || wconv) {  // with EC the epilogue warps certify the A tile
+          // this CTA's split A tile of the stage has landed
+          ok = mbar_wait(full_b(so), (g / C::NSO) & 1, ab, 0x40, g);
+          if (!__all_sync(0xffffffffu, ok)) {
+            stop = true;
+            break;
+          }
         }
         if constexpr ((DIST == kRademacher || DIST == kMixed) && PAIR) {
-          // FP32 A: split it here (the sign bits leave the workers idle)
-          if (ig.pr->conv_inline)
-            convert_stage<C>(smem + C::OFF_B + so * C::OPB, ig.cols, wt);
+          static_assert(C::GROUP_THREADS == 128, "a worker group is one 4-warp set");
+          if (wconv) convert_stage(smem + C::OFF_B + so * C::OPB, ig.cols, wt);
         }
         fence_proxy_async_smem();  // the S tile is read by the tensor core
         __syncwarp();
@@ -1737,11 +1886,11 @@ int num_sms_tc() {
   return sms;
 }
 
-template <int DIST, bool PAIR, bool NARROW = false>
+template <int DIST, bool PAIR, bool NARROW = false, bool EC = false>
 cudaError_t set_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST, PAIR, NARROW>,
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_bf16x2_left<DIST, PAIR, NARROW, EC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg<PAIR, NARROW>::SMEM);
   if (e == cudaSuccess) done = true;
@@ -1876,6 +2025,18 @@ LeftPlan plan_left(const GemmShape& s) {
   return pl;
 }
 
+// Whether a problem on pairs splits its FP32 A inside the sketch kernel.
+// Rademacher: always (the workers do it; their sign bits leave them idle).
+// Gaussian and uniform: the epilogue warps do it, once per 256-row pair tile
+// of k that reads the A tile, while the split pass splits it once; on the
+// 2^20 x 512, k = 2048 sketch (8 pair tiles) the in-kernel split cost 0.9 ms
+// of issue slots against the split pass's 0.65 ms, so only problems with at
+// most 4 pair tiles of k (k <= 1024) split A in the kernel.
+constexpr int64_t kInlineSplitMaxTiles = 4;
+bool inline_split(int dist, const LeftPlan& pl) {
+  return pl.pair && (dist == kRademacher || pl.tiles_p <= kInlineSplitMaxTiles);
+}
+
 // Split pass of one sketch (A rows 16-byte aligned, lda a multiple of 4).
 cudaError_t split_launch_one(const float* A, int64_t lda, int64_t m, int64_t n, void* H,
                              cudaStream_t st) {
@@ -1961,9 +2122,9 @@ LeftSched device_sched(const HostSched& hs, void* dbuf, int* status,
   return sc;
 }
 
-template <int DIST, bool PAIR, bool NARROW = false>
+template <int DIST, bool PAIR, bool NARROW = false, bool EC = false>
 cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
-  cudaError_t e = set_smem_attr<DIST, PAIR, NARROW>();
+  cudaError_t e = set_smem_attr<DIST, PAIR, NARROW, EC>();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(sc.claim, 0, sizeof(int), st);  // the work list starts unclaimed
   if (e != cudaSuccess) return e;
@@ -1971,15 +2132,20 @@ cudaError_t launch_left(const LeftSched& sc, int64_t units, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
   fill_config<PAIR>(&cfg, attr, dim3(static_cast<unsigned>(units * (PAIR ? 2 : 1)), 1, 1), st);
   cfg.dynamicSmemBytes = Cfg<PAIR, NARROW>::SMEM;
-  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR, NARROW>, sc);
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_left<DIST, PAIR, NARROW, EC>, sc);
 }
 
+// ec: Gaussian or uniform sketch on pairs whose A the epilogue warps split
 template <bool PAIR>
-cudaError_t launch_left_dist(int dist, const LeftSched& sc, int64_t units, cudaStream_t st) {
+cudaError_t launch_left_dist(int dist, const LeftSched& sc, int64_t units, cudaStream_t st,
+                             bool ec = false) {
   if (dist == kStored) return launch_left<kStored, PAIR>(sc, units, st);
   if (dist == kRademacher) return launch_left<kRademacher, PAIR>(sc, units, st);
-  if (dist == kUniform) return launch_left<kUniform, PAIR>(sc, units, st);
-  return launch_left<kGaussian, PAIR>(sc, units, st);
+  if (dist == kUniform)
+    return ec ? launch_left<kUniform, PAIR, false, PAIR>(sc, units, st)
+              : launch_left<kUniform, PAIR>(sc, units, st);
+  return ec ? launch_left<kGaussian, PAIR, false, PAIR>(sc, units, st)
+            : launch_left<kGaussian, PAIR>(sc, units, st);
 }
 
 // The split A of an m x n problem as a 4D tensor {64 columns, m rows,
@@ -2062,8 +2228,8 @@ int encode_fp32_map(CUtensorMap* map, const float* A, int64_t m, int64_t n, int6
 }
 
 // A_inline: FP32 A (row stride lda) that the kernel splits in place instead
-// of reading the split pass's halves from H (Rademacher problems on CTA
-// pairs, A passing fp32_map_ok), or null.
+// of reading the split pass's halves from H (problems on CTA pairs whose A
+// passes fp32_map_ok), or null.
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
                   float* part, uint64_t seed, int dist, const float* A_inline = nullptr,
                   int64_t lda = 0) {
@@ -2439,10 +2605,9 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
   const int64_t units = pl.pair ? pair_slots() / 2 : num_sms_tc();
   HostSched hs;
   hs.probs.resize(1);
-  // Rademacher pair sketches split A inside the kernel (their workers are
-  // otherwise idle); the others read the halves the split pass writes
-  const bool conv =
-      S_stored == nullptr && h->dist == kRademacher && pl.pair && fp32_map_ok(A, lda);
+  // Pair sketches split A inside the kernel where inline_split says so;
+  // single CTAs and the stored-S mode read the halves the split pass writes
+  const bool conv = S_stored == nullptr && inline_split(h->dist, pl) && fp32_map_ok(A, lda);
   if (!fill_problem(&hs.probs[0], pl, s, H, part, h->seed, h->dist, conv ? A : nullptr, lda))
     return cudaErrorInvalidValue;
   if (S_stored && !encode_stored_map(&hs.probs[0].smap, S_stored, s.P, s.L, lds))
@@ -2465,7 +2630,7 @@ cudaError_t tc_sketch_left(const sk_sketch* h, const GemmShape& s, const float* 
   cudaError_t e = conv ? cudaSuccess : split_launch_one(A, lda, s.L, s.Q, H, st);
   if (e != cudaSuccess) return e;
   const int mode = S_stored ? kStored : h->dist;
-  e = pl.pair ? launch_left_dist<true>(mode, sc, nunits, st)
+  e = pl.pair ? launch_left_dist<true>(mode, sc, nunits, st, conv && h->dist != kRademacher)
               : launch_left_dist<false>(mode, sc, nunits, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
@@ -2499,6 +2664,7 @@ struct PlannedBatch {
   int64_t units = 0;
   int launches = 0;                // kernels of one run: split (if any), sketch, reduce
   bool narrow = false;             // launched with the 8-stage narrow ring
+  bool econv = false;              // the epilogue warps split some member's A
 };
 
 LeftPlan member_plan(const BatchMember& mb, const BatchShape& bs, GemmShape* shape) {
@@ -2541,6 +2707,7 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
   if (arena == nullptr) return true;  // sizing pass
   pb->hs = HostSched();
   pb->hs.probs.resize(count);
+  pb->econv = false;
   pb->red.clear();
   pb->splits.clear();
   pb->prefix.assign(1, 0);
@@ -2549,11 +2716,12 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
     const BatchMember& mb = mbs[i];
     uint8_t* w = mb.ws ? static_cast<uint8_t*>(mb.ws) : arena + ws_off[i];
     float* part = reinterpret_cast<float*>(w + split_bytes(mb.m, mb.n));
-    // Rademacher members split A inside the sketch kernel (their workers are
-    // otherwise idle); the others (and members whose split is already made)
-    // read the halves
-    const bool conv = !mb.split_ready && mb.dist == kRademacher && plans[i].pair &&
+    // members split A inside the sketch kernel where inline_split says so
+    // (Rademacher: the workers; Gaussian and uniform: the epilogue warps); the
+    // others (and members whose split is already made) read the halves
+    const bool conv = !mb.split_ready && inline_split(mb.dist, plans[i]) &&
                       fp32_map_ok(mb.A, mb.lda);
+    if (conv && mb.dist != kRademacher) pb->econv = true;
     if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], w, part, mb.seed, mb.dist,
                       conv ? mb.A : nullptr, mb.lda))
       return false;
@@ -2660,8 +2828,11 @@ cudaError_t launch_plan(const PlannedBatch& pb, const BatchArena& ar, cudaStream
     count_launches(1);
   }
   const LeftSched sc = device_sched(pb.hs, ar.d_buf, ar.d_status);
-  const cudaError_t e = pb.narrow ? launch_left<kMixed, true, true>(sc, pb.units, st)
-                                  : launch_left<kMixed, true, false>(sc, pb.units, st);
+  const cudaError_t e =
+      pb.narrow ? (pb.econv ? launch_left<kMixed, true, true, true>(sc, pb.units, st)
+                            : launch_left<kMixed, true, true>(sc, pb.units, st))
+                : (pb.econv ? launch_left<kMixed, true, false, true>(sc, pb.units, st)
+                            : launch_left<kMixed, true, false>(sc, pb.units, st));
   if (e != cudaSuccess) return e;
   count_launches(1);
   return splitk_reduce_batched(reinterpret_cast<const ReduceDesc*>(b + pb.off_red),

@@ -47,9 +47,15 @@ def run_left(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
 
 SHAPES = [(128, 4096, 512), (64, 4096, 256), (100, 1000, 48), (130, 777, 300), (1, 16, 16),
           (3, 5, 7), (256, 70000, 1000), (2048, 65536, 512), (200, 300000, 20),
-          # CTA pairs with n a multiple of 32 (the Rademacher kernel splits A in
-          # place): ragged m, a partly filled second column tile, 96 columns
-          (384, 10007, 544), (256, 3000, 96)]
+          # CTA pairs split A in place (one 3D box per stage when n is a
+          # multiple of 32, else a 2D box per 32 columns): ragged m, a partly
+          # filled second column tile, 96 columns, a chain longer than the
+          # item (m below one chain), n = 40 (one chunk per CTA: the second
+          # set of converting warps idle)
+          (384, 10007, 544), (256, 3000, 96), (512, 1500, 256), (256, 20000, 40),
+          # 4 and 5 pair tiles of k: the last Gaussian sketch that splits A in
+          # the kernel, the first that runs the split pass
+          (1024, 9000, 256), (1280, 9000, 256)]
 
 
 @pytest.mark.parametrize("dist", [R, G])
@@ -63,10 +69,11 @@ def test_left_bf16x2_matches_oracle(P, orc, dist, k, m, n):
     assert err <= TOL, err
 
 
-def test_left_bf16x2_uniform(P, orc):
-    A = _A(3000, 64, 5)
-    got = run_left(P, 11, U, 96, A)
-    assert rel_frob(got, orc.apply_left(11, U, BF16, 96, A.numpy())) <= TOL
+@pytest.mark.parametrize("k,m,n", [(96, 3000, 64), (300, 5000, 200)])  # one CTA; pairs
+def test_left_bf16x2_uniform(P, orc, k, m, n):
+    A = _A(m, n, 5)
+    got = run_left(P, 11, U, k, A)
+    assert rel_frob(got, orc.apply_left(11, U, BF16, k, A.numpy())) <= TOL
 
 
 @pytest.mark.parametrize("dist", [R, G])
@@ -77,11 +84,13 @@ def test_identity_gives_scaled_bf16_matrix_exactly(P, orc, dist):
     np.testing.assert_array_equal(got, ref.astype(np.float32))
 
 
-def test_rademacher_in_place_split_with_padded_rows(P, orc):
-    # lda > n: the FP32 tile the kernel splits in place is read with the row pitch
+@pytest.mark.parametrize("dist", [R, G])
+def test_in_place_split_with_padded_rows(P, orc, dist):
+    # lda > n: the FP32 tile the kernel splits in place (Rademacher: the
+    # workers; Gaussian: the epilogue warps) is read with the row pitch
     A = _A(5003, 160, 9)
-    got = run_left(P, 21, R, 300, A, lda=176, ldy=164)
-    assert rel_frob(got, orc.apply_left(21, R, BF16, 300, A.numpy())) <= TOL
+    got = run_left(P, 21, dist, 300, A, lda=176, ldy=164)
+    assert rel_frob(got, orc.apply_left(21, dist, BF16, 300, A.numpy())) <= TOL
 
 
 def test_rademacher_bf16x2_agrees_with_fp32_form(P):
@@ -157,8 +166,9 @@ def test_full_size_tall_skinny_sampled(P, orc, dist):
 @pytest.mark.parametrize("dist", [R, G])
 def test_full_size_ragged_sampled(P, orc, dist):
     # near-full size with a ragged tail everywhere: m not a multiple of a
-    # stage or a split of m, n = 500 (second column tile partly filled, no
-    # in-place split), k = 2000 (last 256-row tile of k partly filled)
+    # stage or a split of m, n = 500 (second column tile partly filled, A
+    # split in place by 32-column boxes), k = 2000 (last 256-row tile of k
+    # partly filled)
     m, n, k = (1 << 20) - 37, 500, 2000
     A, Y = _full_size_left(P, dist, m, n, k, 2, 500)
     cols = np.array([0, 255, 256, 480, 499])

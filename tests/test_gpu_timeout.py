@@ -24,10 +24,11 @@ LIMIT_NS = 20_000_000  # 20 ms: a healthy stage of these sizes takes microsecond
 
 # Wait sites (role * 16 + barrier) that depend on the stage whose copy is never
 # issued: the MMA issuer waiting for that stage's operands (0x22), a worker
-# waiting for its A tile (0x40), an epilogue waiting for the accumulation chain
-# that needs it (0x34), the TMA producer or a worker waiting for a ring slot
-# that stage holds (0x13, 0x43).
-DEPENDENT_SITES = {0x22, 0x40, 0x34, 0x13, 0x43}
+# waiting for its A tile (0x40; one CTA), an epilogue warp waiting for the A
+# tile it splits in place (0x30; Gaussian sketches on CTA pairs) or for the
+# accumulation chain that needs it (0x34), the TMA producer or a worker
+# waiting for a ring slot that stage holds (0x13, 0x43).
+DEPENDENT_SITES = {0x22, 0x40, 0x30, 0x34, 0x13, 0x43}
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +66,7 @@ def test_bounded_wait_gives_up_and_the_handle_recovers(P, orc, k):
         elapsed = time.perf_counter() - t0
         assert words[0] == 4, words  # SK_ETIMEOUT
         assert words[1] in DEPENDENT_SITES, hex(words[1])
-        if words[1] in (0x22, 0x40):
+        if words[1] in (0x22, 0x40, 0x30):
             assert words[2] == stall, words
         assert words[3] >= 0
         assert elapsed < 5.0, elapsed  # the limit plus bounded drains, not a hang
