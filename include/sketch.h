@@ -267,7 +267,7 @@ sk_status sk_batch_add(sk_batch_handle b, sk_handle h, const float* A, int64_t m
  * after a change plans the work (with the configuration sk_batch_tune or
  * sk_batch_set_config chose, else one from the tuning cache file named by
  * the environment variable SK_TUNE_CACHE, else the default: items of 512
- * stages, 512-column tiles, 5-stage ring), allocates the batch's device
+ * stages, 512-column tiles, 4-stage ring), allocates the batch's device
  * buffers and captures the graph; later runs replay it.
  * Errors: SK_EINVAL (empty batch), SK_ENOMEM, SK_ECUDA. */
 sk_status sk_batch_run(sk_batch_handle b, void* stream);
@@ -276,7 +276,7 @@ sk_status sk_batch_run(sk_batch_handle b, void* stream);
  * `stream`, synchronising) for every candidate and keep the fastest.  The
  * candidates combine the tile shape (output tiles of at most 512 columns,
  * two MMA instructions per K step, or of at most 256), the pipeline depth
- * (operand ring of 5 stages, or of 8 half-width stages, which needs tiles of
+ * (operand ring of 4 stages, or of 8 half-width stages, which needs tiles of
  * at most 256 columns) and the item length (128 to 4096 stages of 16 rows of
  * m per work item).  *chosen (may be NULL) receives the item length;
  * sk_batch_config reports the whole choice.  When SK_TUNE_CACHE names a
@@ -286,7 +286,7 @@ sk_status sk_batch_tune(sk_batch_handle b, void* stream, int64_t* chosen);
 
 /* Fix the configuration of later runs instead of tuning: item_stages >= 1
  * (16-row units of m per work item), tile_cols 512 or 256 (widest output
- * tile), ring_stages 5 or 8 (8 requires tile_cols 256).  Invalidates the
+ * tile), ring_stages 4 or 8 (8 requires tile_cols 256).  Invalidates the
  * plan and graph.  Errors: SK_EINVAL. */
 sk_status sk_batch_set_config(sk_batch_handle b, int64_t item_stages, int32_t tile_cols,
                               int32_t ring_stages);

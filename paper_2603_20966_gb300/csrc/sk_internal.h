@@ -73,6 +73,7 @@ struct ReduceDesc {
   const float* part;
   float* Y;
   int64_t P, Q, ldy;
+  int64_t ldp;  // partial row stride (>= Q): part[(z P + r) ldp + c]
   int splits;
   float scale;
 };

@@ -281,11 +281,13 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int6
 __global__ void k_splitk_reduce_batched(const ReduceDesc* __restrict__ desc) {
   const ReduceDesc d = desc[blockIdx.y];
   const int64_t total = d.P * d.Q;
+  const int64_t zstride = d.P * d.ldp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int z = 0; z < d.splits; ++z) s = __fadd_rn(s, d.part[(int64_t)z * total + i]);
     const int64_t r = i / d.Q, c = i % d.Q;
+    const float* p = d.part + r * d.ldp + c;
+    float s = 0.f;
+    for (int z = 0; z < d.splits; ++z) s = __fadd_rn(s, p[(int64_t)z * zstride]);
     d.Y[r * d.ldy + c] = __fmul_rn(d.scale, s);
   }
 }

@@ -88,11 +88,16 @@ constexpr int NTHREADS = 32 * (WARP_WORK0 + NUM_WORK_WARPS);  // 832
 // rows padded to 20 floats (16-byte aligned, few bank conflicts).
 constexpr int EPI_PITCH = 20;
 constexpr uint32_t EPI_TILE = 32 * EPI_PITCH * 4;
+// Staging tile of a TMA drain: 32 accumulator rows x 32 columns (128 B per
+// row, the 128-byte swizzle of the partial's tensor map).
+constexpr uint32_t DRAIN_TILE = 32 * 32 * 4;
 
 // Per-CTA buffers of the left kernel.  A CTA of a pair holds NT/2 columns of
 // each split A tile.  NARROW (pairs only, batches whose tiles all have at most
 // 256 columns): half-width split A slots, so the operand ring is 8 stages
-// deep instead of 5.
+// deep instead of 4.  TDRAIN (all but NARROW): each epilogue warp has two
+// 4 KB staging tiles from which the TMA adds a drained accumulator chain into
+// the partial (see drain_chain_tma); a narrow ring has no room for them.
 template <bool PAIR, bool NARROW = false>
 struct Cfg {
   static_assert(PAIR || !NARROW, "narrow rings are a pair configuration");
@@ -104,13 +109,15 @@ struct Cfg {
   static constexpr int NGROUPS = PAIR ? 4 : 2;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NSO = NARROW ? 8 : PAIR ? 5 : 2;     // operand stages
+  static constexpr int NSO = NARROW ? 8 : PAIR ? 4 : 2;     // operand stages
+  static constexpr bool TDRAIN = !NARROW;
   static constexpr uint32_t OPB = 2u * COLS * LK * 2u;      // hi and lo tiles of a stage
   static constexpr uint32_t OPS = BM * LK * 2;              // S tile: KSTEPS slabs of 16
   static constexpr uint32_t OFF_B = 0;
   static constexpr uint32_t OFF_S = OFF_B + NSO * OPB;
-  static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;    // epilogue transpose tiles
-  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
+  static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;    // epilogue tiles, per warp:
+  static constexpr uint32_t EPI_BYTES = TDRAIN ? 2 * DRAIN_TILE : EPI_TILE;
+  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_BYTES;
   static constexpr uint32_t NUM_BARS = 3 * NSO + 3 + 2 * IQ;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;  // abort flag, TMEM slot, item queue
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 4 * IQ + 1024;  // + slack for 1 KB alignment
@@ -121,6 +128,8 @@ struct Cfg {
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(NGROUPS <= NSO, "worker groups vs ring depth");
   static_assert(OPB % 1024 == 0, "split tiles start on swizzle-atom boundaries");
+  static_assert(!TDRAIN || OFF_EPI % 1024 == 0, "staging tiles on swizzle-atom boundaries");
+  static_assert(EPI_BYTES >= EPI_TILE, "the transpose tile fits the warp's area");
 };
 
 // K-major no-swizzle operand layout (16-element K slab): core matrix
@@ -145,8 +154,9 @@ constexpr uint32_t B_KSTEP = BK * HCHUNK * 2;       // 2048: next 16 rows of m
 struct alignas(128) LeftProblem {
   CUtensorMap map;   // split A: {64 columns, m rows, chunks, hi/lo}, box {64, 32, cols/64, 2}
   CUtensorMap smap;  // stored S (kStored only): the S tile of a stage in its operand layout
-  float* part;      // partials [splits][P][Q] of this problem
+  float* part;      // partials [splits][P][ldp] of this problem (columns Q .. ldp-1 unused)
   int64_t P, Q, L;  // P = k, Q = n, L = m
+  int64_t ldp;      // partial row stride, >= Q
   int64_t chunk;    // contracted length per split (multiple of LK)
   int nt;           // output columns per tile: a multiple of 128 (pairs) or 64 up to 256, or 512
   int dist;         // sk_dist of S
@@ -161,6 +171,12 @@ struct alignas(128) LeftProblem {
   // them
   int conv_inline;
   CUtensorMap amap;
+  // tma_drain: the partials as a 3D FP32 tensor {Q, P, splits} (row stride
+  // ldp) with boxes of 32 columns x 32 rows and the 128-byte swizzle
+  // (`pmap`); the epilogue drains through the TMA (needs ldp % 4 == 0 and part
+  // 16-byte aligned)
+  int tma_drain;
+  CUtensorMap pmap;
 };
 
 // A unit of work: tile (tp, tq) of split z of problem `prob`.  With pairs,
@@ -471,6 +487,79 @@ __device__ __forceinline__ void gen_stage(uint8_t* sdst, const ItemGeo& g, const
   }
 }
 
+// One accumulator drain by an epilogue warp of the left kernel through the
+// TMA: wait until chain gc has finished, and for each of the warp's 32-column
+// chunks of its TMEM lane quarter, read the chunk (lane = row), write it into
+// one of the warp's two staging tiles (row r at 128 r, its 16-byte unit u at
+// u ^ (r mod 8): the 128-byte swizzle, and no bank conflict as the 8 lanes of
+// a phase write 8 different units), and let lane 0 hand the tile to the TMA,
+// which stores it into the item's partial (first chain) or adds it there
+// element by element; boxes reaching past P rows or Q columns are clipped.
+// The accumulator is released as soon as its last chunk is read: the global
+// writes no longer hold up the next chain.  The adds of one address stay in
+// chain order, hence deterministic: lane 0 waits until its previous chain's
+// copies have completed before issuing this chain's, and a staging tile is
+// rewritten only after the copy two chunks back has read it.
+template <bool PAIR>
+__device__ __noinline__ bool drain_chain_tma(uint32_t tmem, int quarter, int colset,
+                                             uint32_t stage_u32, float* stage, const ItemGeo ig,
+                                             int z, bool first, uint32_t acc_full,
+                                             uint32_t lead_acc_empty, int gc, const Abort ab) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) bulk_wait<0>();
+  const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
+  if (!__all_sync(0xffffffffu, ok)) return false;  // tcgen05.ld below is warp-collective
+  tc_fence_after();
+  const int32_t y = static_cast<int32_t>(ig.p0 + quarter * 32);
+  const uint32_t sw = static_cast<uint32_t>(lane) & 7u;
+  int nb = 0;
+  for (int ci = colset; ci * 32 < (ig.nmma - 1) * 256 + ig.nh; ci += 2, ++nb) {
+    uint32_t v[32];
+    tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(ci * 32),
+              v);
+    tmem_ld_wait();
+    // TMEM column h*256 + c holds B row c of instruction h (pair: rows c < bh
+    // the even CTA's tile columns h*bh + c, the others the odd CTA's
+    // cols + h*bh + (c - bh)); bh is a multiple of 64, so a chunk of 32 is
+    // contiguous in the tile
+    const int h = (ci * 32) >> 8;
+    const int c = (ci * 32) & 255;
+    const int tn =
+        PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh)) : ci * 32;
+    const uint32_t b = static_cast<uint32_t>(nb & 1);
+    if (nb >= 2) {
+      if (lane == 0) bulk_wait_read<1>();
+      __syncwarp();
+    }
+    float* row = stage + b * (DRAIN_TILE / 4) + lane * 32;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(row + ((static_cast<uint32_t>(q) ^ sw) << 2)) =
+          make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+    fence_proxy_async_smem();  // the tile is read by the TMA
+    __syncwarp();
+    if (lane == 0) {
+      const int32_t x = static_cast<int32_t>(ig.q0 + tn);
+      const uint32_t src = stage_u32 + b * DRAIN_TILE;
+      if (first)
+        tma_store_3d(&ig.pr->pmap, src, x, y, z);
+      else
+        tma_reduce_add_3d(&ig.pr->pmap, src, x, y, z);
+      bulk_commit();
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) {
+    if (PAIR)
+      mbar_arrive_cluster(lead_acc_empty);
+    else
+      mbar_arrive(lead_acc_empty);
+  }
+  return true;
+}
+
 // One accumulator drain by an epilogue warp of the left kernel (the steps of
 // the kernel's own epilogue loop): wait until chain gc has finished, read the
 // warp's TMEM lane quarter x its 32-column chunks, write them through the
@@ -485,8 +574,8 @@ __device__ __noinline__ bool drain_chain_left(uint32_t tmem, int quarter, int co
   const int lane = threadIdx.x & 31;
   const int rsub = lane >> 2;       // row within a group of 8 (read side)
   const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
-  const int64_t P = ig.pr->P, Q = ig.pr->Q;
-  const bool vec_ok = (Q % 4) == 0;
+  const int64_t P = ig.pr->P, Q = ig.pr->Q, ldp = ig.pr->ldp;
+  const bool vec_ok = (ldp % 4) == 0;
   const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
   if (!__all_sync(0xffffffffu, ok)) return false;  // tcgen05.ld below is warp-collective
   tc_fence_after();
@@ -517,7 +606,7 @@ __device__ __noinline__ bool drain_chain_left(uint32_t tmem, int quarter, int co
         const int64_t gp = ig.p0 + quarter * 32 + rr;
         const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
         if (c < ig.nh && gp < P) {
-          float* d = part_item + gp * Q + tn;
+          float* d = part_item + gp * ldp + tn;
           if (vec_ok && col + 4 <= Q) {
             if (first)
               *reinterpret_cast<float4*>(d) = a;
@@ -798,13 +887,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp < WARP_WORK0) {
     // ---- epilogue: add each finished chain into the item's FP32 partial ----
-    // A warp reads 32 accumulator rows (its TMEM lane quarter) x 32 columns,
-    // then writes them through a transpose tile so that every global store /
-    // reduction instruction covers 64-byte pieces of 8 rows instead of 16
-    // bytes of 32 rows.
+    // Problems with a TMA map of their partials drain through the TMA
+    // (drain_chain_tma); otherwise a warp reads 32 accumulator rows (its TMEM
+    // lane quarter) x 32 columns, then writes them through a transpose tile so
+    // that every global store / reduction instruction covers 64-byte pieces
+    // of 8 rows instead of 16 bytes of 32 rows.
     const int quarter = warp & 3;
     const int colset = (warp - WARP_EPI0) >> 2;  // 0 or 1: even / odd 32-column chunks
-    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * EPI_TILE);
+    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_BYTES);
+    const uint32_t tile_u32 = smem_u32(tile);
     const int rsub = lane >> 2;       // row within a group of 8 (read side)
     const int csub = (lane & 3) * 4;  // first of 4 columns (read side)
     if constexpr (EC) {
@@ -822,7 +913,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       auto drain_pending = [&]() -> bool {
         const ItemGeo pg = item_geo<PAIR>(sc, pend, rank);
         const LeftItem it = sc.items[pend];
-        float* part_item = pg.pr->part + static_cast<int64_t>(it.z) * pg.pr->P * pg.pr->Q + pg.q0;
+        if (C::TDRAIN && pg.pr->tma_drain)
+          return drain_chain_tma<PAIR>(tmem, quarter, colset, tile_u32, tile, pg, it.z,
+                                       pend_first, acc_full, lead_acc_empty, gc++, ab);
+        float* part_item =
+            pg.pr->part + static_cast<int64_t>(it.z) * pg.pr->P * pg.pr->ldp + pg.q0;
         return drain_chain_left<PAIR>(tmem, quarter, colset, tile, pg, part_item, pend_first,
                                       acc_full, lead_acc_empty, gc++, ab);
       };
@@ -859,6 +954,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       if (pend >= 0 && !stop) drain_pending();
+      if (C::TDRAIN && lane == 0) bulk_wait<0>();  // the last copies have completed
     } else {
       int gc = 0;
       bool stop = false;
@@ -867,10 +963,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (idx < 0) break;
         const ItemGeo ig = item_geo<PAIR>(sc, idx, rank);
         const LeftItem it = sc.items[idx];
-        const int64_t P = ig.pr->P, Q = ig.pr->Q;
-        float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * Q + ig.q0;
-        const bool vec_ok = (Q % 4) == 0;
+        const int64_t P = ig.pr->P, Q = ig.pr->Q, ldp = ig.pr->ldp;
+        float* part_item = ig.pr->part + static_cast<int64_t>(it.z) * P * ldp + ig.q0;
+        const bool vec_ok = (ldp % 4) == 0;
         const int nchains = (ig.nsteps + ig.coff + ig.chain - 1) / ig.chain;
+        if (C::TDRAIN && ig.pr->tma_drain) {
+          for (int c0 = 0; c0 < nchains; ++c0) {
+            if (!drain_chain_tma<PAIR>(tmem, quarter, colset, tile_u32, tile, ig, it.z, c0 == 0,
+                                       acc_full, lead_acc_empty, gc++, ab)) {
+              stop = true;
+              break;
+            }
+          }
+          continue;
+        }
         for (int c0 = 0; c0 < nchains; ++c0, ++gc) {
           const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
           if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld below is warp-collective
@@ -887,10 +993,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           static_cast<uint32_t>(ci * 32),
                       v);
             tmem_ld_wait();
-  #pragma unroll
+#pragma unroll
             for (int half = 0; half < 2; ++half) {
               // lane = accumulator row: its 16 columns into the tile
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < 4; ++q)
                 *reinterpret_cast<float4*>(tile + lane * EPI_PITCH + 4 * q) =
                     make_float4(__uint_as_float(v[16 * half + 4 * q]),
@@ -905,13 +1011,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int tn = PAIR ? (c < ig.bh ? h * ig.bh + c : ig.cols + h * ig.bh + (c - ig.bh))
                                   : tcol;
               const int64_t col = ig.q0 + tn;
-  #pragma unroll
+#pragma unroll
               for (int pass = 0; pass < 4; ++pass) {
                 const int rr = 8 * pass + rsub;
                 const int64_t gp = ig.p0 + quarter * 32 + rr;
                 const float4 a = *reinterpret_cast<const float4*>(tile + rr * EPI_PITCH + csub);
                 if (c < ig.nh && gp < P) {
-                  float* d = part_item + gp * Q + tn;
+                  float* d = part_item + gp * ldp + tn;
                   if (vec_ok && col + 4 <= Q) {
                     if (c0 == 0)
                       *reinterpret_cast<float4*>(d) = a;
@@ -943,6 +1049,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
+      if (C::TDRAIN && lane == 0) bulk_wait<0>();  // the last copies have completed
     }
   } else {
     // ---- workers: generate this CTA's S tile, hand the stage to the MMA ----
@@ -1049,7 +1156,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // matrices, hi (256 bytes: 8 rows x 2 halves of 8 columns) then lo, so a warp
 // converts one group with no other warp involved, and the MMA reads hi and lo
 // with 512 bytes between 8-row groups.  With no separate staging ring the
-// slots are 20 KB and the ring is 9 stages deep, so up to 144 KB of A per SM
+// slots are 20 KB and the ring is 8 stages deep, so up to 128 KB of A per SM
 // are in flight from HBM.
 // ---------------------------------------------------------------------------
 struct CfgR {
@@ -1057,18 +1164,20 @@ struct CfgR {
   static constexpr int NGROUPS = 4;
   static constexpr int GROUP_WARPS = NUM_WORK_WARPS / NGROUPS;
   static constexpr int GROUP_THREADS = 32 * GROUP_WARPS;
-  static constexpr int NS = 9;                        // stages in the ring
+  static constexpr int NS = 8;                        // stages in the ring
   static constexpr uint32_t OPA = BK * ROWS * 4;      // FP32 A tile = its hi and lo halves
   static constexpr uint32_t ACC_A = OPA / 2;          // hi + lo of one 128-row accumulator
   static constexpr uint32_t GROUP_A = 512;            // one 8-row group, FP32 = hi + lo
   static constexpr uint32_t OPS = 128 * BK * 2;       // this CTA's half of the S tile
   static constexpr uint32_t OFF_A = 0;
   static constexpr uint32_t OFF_S = OFF_A + NS * OPA;
-  // epilogue transpose tiles: 32 rows x 32 columns (pitch 36 floats) per warp
+  // epilogue area per warp: two staging tiles of a TMA drain, or the
+  // transpose tile (32 rows x 32 columns, pitch 36 floats) of the red.add one
   static constexpr int EPI_PITCH_R = 36;
   static constexpr uint32_t EPI_TILE_R = 32 * EPI_PITCH_R * 4;
+  static constexpr uint32_t EPI_BYTES = 2 * DRAIN_TILE;
   static constexpr uint32_t OFF_EPI = OFF_S + NS * OPS;
-  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE_R;
+  static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_BYTES;
   // per slot: A landed, operands ready, slot read by both pairs' MMAs, S rows
   // received from the partner CTA; then the accumulator and drain barriers
   static constexpr uint32_t NUM_BARS = 4 * NS + 3;
@@ -1077,6 +1186,7 @@ struct CfgR {
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(NGROUPS <= NS, "worker groups vs ring depth");
   static_assert(OPA % 1024 == 0 && OPS % 1024 == 0, "slots on 1 KB boundaries");
+  static_assert(OFF_EPI % 1024 == 0 && EPI_BYTES >= EPI_TILE_R, "epilogue tiles");
 };
 
 struct TcRightParams {
@@ -1088,11 +1198,67 @@ struct TcRightParams {
   PhiloxRoundKeys rk;
   int* status;
   uint64_t timeout_ns;
+  int tma_drain;  // the partials' tensor map (kernel parameter tmapP) is valid
 };
+
+// The right kernel's accumulator drain through the TMA, as drain_chain_tma:
+// accumulator j (0, 1) holds rows m0 + 128 j + lane of the warp's TMEM lane
+// quarter and the pair's k rows q0 + c in its columns.
+__device__ __noinline__ bool drain_right_tma(uint32_t tmem, int quarter, int colset,
+                                             uint32_t stage_u32, float* stage,
+                                             const CUtensorMap* pmap, int nq, int64_t m0,
+                                             int64_t q0, int z, bool first, uint32_t acc_full,
+                                             uint32_t lead_acc_empty, int c0, const Abort ab) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) bulk_wait<0>();
+  const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
+  if (!__all_sync(0xffffffffu, ok)) return false;  // tcgen05.ld below is warp-collective
+  tc_fence_after();
+  const int nchunk = (nq + 31) / 32;
+  const uint32_t sw = static_cast<uint32_t>(lane) & 7u;
+  int nb = 0;
+  for (int t = colset; t < 2 * nchunk; t += 2, ++nb) {
+    const int j = t / nchunk;
+    const int ci = t - j * nchunk;
+    uint32_t v[32];
+    tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                  static_cast<uint32_t>(j * nq + ci * 32),
+              v);
+    tmem_ld_wait();
+    const uint32_t b = static_cast<uint32_t>(nb & 1);
+    if (nb >= 2) {
+      if (lane == 0) bulk_wait_read<1>();
+      __syncwarp();
+    }
+    float* row = stage + b * (DRAIN_TILE / 4) + lane * 32;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(row + ((static_cast<uint32_t>(q) ^ sw) << 2)) =
+          make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+    fence_proxy_async_smem();  // the tile is read by the TMA
+    __syncwarp();
+    if (lane == 0) {
+      const int32_t x = static_cast<int32_t>(q0 + ci * 32);
+      const int32_t y = static_cast<int32_t>(m0 + j * 128 + quarter * 32);
+      const uint32_t src = stage_u32 + b * DRAIN_TILE;
+      if (first)
+        tma_store_3d(pmap, src, x, y, z);
+      else
+        tma_reduce_add_3d(pmap, src, x, y, z);
+      bulk_commit();
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
+  return true;
+}
 
 template <int DIST>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_sketch_bf16x2_right(const __grid_constant__ CUtensorMap tmapA, const TcRightParams p) {
+    k_sketch_bf16x2_right(const __grid_constant__ CUtensorMap tmapA,
+                          const __grid_constant__ CUtensorMap tmapP, const TcRightParams p) {
   using C = CfgR;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -1247,10 +1413,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int colset = (warp - WARP_EPI0) >> 2;
     const bool vec_ok = (p.Q % 4) == 0;
     const int nchunk = (nq + 31) / 32;
-    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_TILE_R);
+    float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_BYTES);
     const int rsub = lane >> 3;       // row within a group of 4 (read side)
     const int csub = (lane & 7) * 4;  // first of 4 columns (read side)
-    for (int c0 = 0; c0 < nchains; ++c0) {
+    if (p.tma_drain) {  // through the TMA (partial rows of whole 16-byte units)
+      for (int c0 = 0; c0 < nchains; ++c0)
+        if (!drain_right_tma(tmem, quarter, colset, smem_u32(tile), tile, &tmapP, nq, m0, q0,
+                             static_cast<int>(blockIdx.z), c0 == 0, acc_full, lead_acc_empty, c0,
+                             ab))
+          break;
+      if (lane == 0) bulk_wait<0>();  // the last copies have completed
+    }
+    for (int c0 = 0; c0 < (p.tma_drain ? 0 : nchains); ++c0) {
       const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
@@ -2227,12 +2401,32 @@ int encode_fp32_map(CUtensorMap* map, const float* A, int64_t m, int64_t n, int6
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS ? 2 : 0;
 }
 
+// The FP32 partials [splits][P][ldp] as a 3D tensor {Q, P, splits} with boxes
+// of 32 columns x 32 rows and the 128-byte swizzle, for the epilogue's TMA
+// drain (drain_chain_tma); false when the rows are not 16-byte multiples or
+// the base not 16-byte aligned (the epilogue then writes with red.add).
+bool encode_part_map(CUtensorMap* map, const float* part, int64_t P, int64_t Q, int64_t ldp,
+                     int splits) {
+  if (ldp % 4 != 0 || reinterpret_cast<uintptr_t>(part) % 16 != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return false;
+  const cuuint64_t gdim[3] = {static_cast<cuuint64_t>(Q), static_cast<cuuint64_t>(P),
+                              static_cast<cuuint64_t>(splits)};
+  const cuuint64_t gstride[2] = {static_cast<cuuint64_t>(ldp) * 4,
+                                 static_cast<cuuint64_t>(P) * static_cast<cuuint64_t>(ldp) * 4};
+  const cuuint32_t box[3] = {32, 32, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(part), gdim, gstride,
+             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // A_inline: FP32 A (row stride lda) that the kernel splits in place instead
 // of reading the split pass's halves from H (problems on CTA pairs whose A
 // passes fp32_map_ok), or null.
 bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const void* H,
                   float* part, uint64_t seed, int dist, const float* A_inline = nullptr,
-                  int64_t lda = 0) {
+                  int64_t lda = 0, int64_t ldp = 0) {
   memset(pr, 0, sizeof(*pr));
   if (!encode_split_map(&pr->map, H, s.L, s.Q, pl.pair ? pl.nt / 2 : pl.nt)) return false;
   if (A_inline != nullptr) {
@@ -2249,6 +2443,8 @@ bool fill_problem(LeftProblem* pr, const LeftPlan& pl, const GemmShape& s, const
   pr->dist = dist;
   pr->chain = left_chain_stages(dist);
   pr->key = make_key(seed);
+  pr->ldp = ldp > 0 ? ldp : s.Q;
+  pr->tma_drain = encode_part_map(&pr->pmap, part, s.P, s.Q, pr->ldp, pl.splits) ? 1 : 0;
   return true;
 }
 
@@ -2391,15 +2587,15 @@ int64_t quad_slots() {
 }
 
 template <int DIST>
-cudaError_t launch_right(const CUtensorMap& map, const TcRightParams& p, dim3 grid,
-                         cudaStream_t st) {
+cudaError_t launch_right(const CUtensorMap& map, const CUtensorMap& pmap, const TcRightParams& p,
+                         dim3 grid, cudaStream_t st) {
   cudaError_t e = set_smem_attr_right();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   fill_config<true>(&cfg, attr, grid, st, 4);
   cfg.dynamicSmemBytes = CfgR::SMEM;
-  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_right<DIST>, map, p);
+  return cudaLaunchKernelEx(&cfg, k_sketch_bf16x2_right<DIST>, map, pmap, p);
 }
 
 cudaError_t grow_device(void** buf, size_t* have, size_t need) {
@@ -2476,16 +2672,19 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
   p.part = static_cast<float*>(ws);
+  CUtensorMap pmap;
+  memset(&pmap, 0, sizeof(pmap));
+  p.tma_drain = encode_part_map(&pmap, p.part, s.P, s.Q, s.Q, pl.splits) ? 1 : 0;
   dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
             static_cast<unsigned>(pl.splits));
   prof_mark(h->prof_start, st);
   cudaError_t e;
   if (h->dist == kRademacher)
-    e = launch_right<kRademacher>(map, p, grid, st);
+    e = launch_right<kRademacher>(map, pmap, p, grid, st);
   else if (h->dist == kUniform)
-    e = launch_right<kUniform>(map, p, grid, st);
+    e = launch_right<kUniform>(map, pmap, p, grid, st);
   else
-    e = launch_right<kGaussian>(map, p, grid, st);
+    e = launch_right<kGaussian>(map, pmap, p, grid, st);
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
@@ -2681,8 +2880,13 @@ LeftPlan member_plan(const BatchMember& mb, const BatchShape& bs, GemmShape* sha
   return pl;
 }
 
+// Batch members keep their partials in rows of a multiple of 4 columns, so
+// that every member drains through the TMA.
+int64_t member_ldp(int64_t n) { return (n + 3) / 4 * 4; }
+
 size_t partial_bytes(const LeftPlan& pl, const GemmShape& s) {
-  return (static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float) + 255) / 256 * 256;
+  return (static_cast<size_t>(pl.splits) * s.P * member_ldp(s.Q) * sizeof(float) + 255) / 256 *
+         256;
 }
 
 // Work list of a batch whose arena workspace starts at `arena`; with `arena`
@@ -2723,7 +2927,7 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
                       fp32_map_ok(mb.A, mb.lda);
     if (conv && mb.dist != kRademacher) pb->econv = true;
     if (!fill_problem(&pb->hs.probs[i], plans[i], shapes[i], w, part, mb.seed, mb.dist,
-                      conv ? mb.A : nullptr, mb.lda))
+                      conv ? mb.A : nullptr, mb.lda, member_ldp(mb.n)))
       return false;
     if (!mb.split_ready && !conv) {
       SplitDesc d;
@@ -2742,6 +2946,7 @@ bool plan_members(const BatchMember* mbs, size_t count, const BatchShape& bs, ui
     r.Y = mb.Y;
     r.P = mb.k;
     r.Q = mb.n;
+    r.ldp = member_ldp(mb.n);
     r.ldy = mb.ldy;
     r.splits = plans[i].splits;
     r.scale = mb.scale;
@@ -3125,7 +3330,7 @@ sk_status sk_batch_set_config(sk_batch_handle b, int64_t item_stages, int32_t ti
                               int32_t ring_stages) {
   if (!b || item_stages < 1 || item_stages >= (int64_t(1) << 20)) return SK_EINVAL;
   if (tile_cols != 256 && tile_cols != 512) return SK_EINVAL;
-  if (ring_stages != 5 && ring_stages != 8) return SK_EINVAL;
+  if (ring_stages != 4 && ring_stages != 8) return SK_EINVAL;
   if (ring_stages == 8 && tile_cols != 256) return SK_EINVAL;
   batch_invalidate(b);
   b->shape.item_stages = item_stages;
@@ -3142,7 +3347,7 @@ sk_status sk_batch_config(sk_batch_handle b, int64_t* item_stages, int32_t* tile
   if (!b->chosen && !decode_shape(cache_lookup(batch_signature(b)), &bs)) bs = sk::BatchShape();
   if (item_stages) *item_stages = bs.item_stages;
   if (tile_cols) *tile_cols = bs.max_nt;
-  if (ring_stages) *ring_stages = bs.narrow ? 8 : 5;
+  if (ring_stages) *ring_stages = bs.narrow ? 8 : 4;
   return SK_OK;
 }
 

@@ -116,7 +116,7 @@ def test_batch_agrees_with_single_calls(P):
 
 # (item stages, tile columns, ring stages): the kernel configurations the
 # autotuner chooses from
-CONFIGS = [(512, 512, 5), (256, 256, 5), (1024, 256, 8)]
+CONFIGS = [(512, 512, 4), (256, 256, 4), (1024, 256, 8)]
 
 
 def _batch_cfg(P, data, cfg):
@@ -153,10 +153,10 @@ def test_every_configuration_matches_oracle(P, orc, cfg):
 def test_set_config_rejects_bad_values(P):
     b = P.sk_batch_create()
     try:
-        for bad in [(0, 512, 5), (512, 384, 5), (512, 512, 6), (512, 512, 8)]:
+        for bad in [(0, 512, 4), (512, 384, 4), (512, 512, 5), (512, 512, 8)]:
             with pytest.raises(P.SketchError):
                 P.sk_batch_set_config(b, *bad)
-        assert P.sk_batch_config(b) == {"item_stages": 512, "tile_cols": 512, "ring_stages": 5}
+        assert P.sk_batch_config(b) == {"item_stages": 512, "tile_cols": 512, "ring_stages": 4}
     finally:
         P.sk_batch_destroy(b)
 
@@ -169,8 +169,8 @@ def test_autotune_then_correct(P, orc, tmp_path, monkeypatch):
         assert chosen in (128, 256, 512, 1024, 2048, 4096)
         cfg = P.sk_batch_config(b)
         assert cfg["item_stages"] == chosen
-        assert cfg["tile_cols"] in (256, 512) and cfg["ring_stages"] in (5, 8)
-        assert cfg["ring_stages"] == 5 or cfg["tile_cols"] == 256
+        assert cfg["tile_cols"] in (256, 512) and cfg["ring_stages"] in (4, 8)
+        assert cfg["ring_stages"] == 4 or cfg["tile_cols"] == 256
         assert (tmp_path / "tune.json").exists()
         for d in data:
             A = d["A"][:, :d["n"]].cpu().numpy()
