@@ -1157,7 +1157,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // converts one group with no other warp involved, and the MMA reads hi and lo
 // with 512 bytes between 8-row groups.  With no separate staging ring the
 // slots are 20 KB and the ring is 8 stages deep, so up to 128 KB of A per SM
-// are in flight from HBM.
+// are in flight from HBM.  The kernel is persistent: as many clusters as can
+// be resident each run every NC-th item of the work list, with ring slots,
+// barrier phases and chains counted across items, so the next item's copies
+// and S tiles are under way while the last chain of the previous one drains.
 // ---------------------------------------------------------------------------
 struct CfgR {
   static constexpr int ROWS = 256;  // rows of A per CTA (two 128-row accumulators)
@@ -1199,6 +1202,16 @@ struct TcRightParams {
   int* status;
   uint64_t timeout_ns;
   int tma_drain;  // the partials' tensor map (kernel parameter tmapP) is valid
+  // work list: items (cluster block of 4 x 256 rows of m, pair tile of k,
+  // split of n), split fastest
+  int nitems, tiles_q, splits;
+};
+
+// One item of the persistent right kernel, as seen by one CTA.
+struct RightItem {
+  int64_t m0, q0, g0;  // first row of A, of the pair's k rows, of this CTA's S rows
+  int64_t lbeg, lend;  // range of n
+  int nsteps, nchains, z;
 };
 
 // The right kernel's accumulator drain through the TMA, as drain_chain_tma:
@@ -1296,13 +1309,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int gh = nq / 2;                                       // S rows this CTA holds
   const int gq = gh / 2;                                       // ... and generates
   const int gbase = static_cast<int>(pairi) * gq;              // from this row of them
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * C::ROWS;  // this CTA's rows of A
-  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nq;       // the pair's k rows
-  const int64_t g0 = q0 + static_cast<int64_t>(rank) * gh;        // this CTA's S rows
-  const int64_t lbeg = static_cast<int64_t>(blockIdx.z) * p.chunk;
-  const int64_t lend = min(p.L, lbeg + p.chunk);
-  const int nsteps = static_cast<int>((lend - lbeg + BK - 1) / BK);
-  const int nchains = (nsteps + CHAIN - 1) / CHAIN;
+  // Persistent: cluster c of the grid runs items c, c + NC, ... (NC
+  // clusters), every CTA of the cluster the same list; an item is (block of
+  // 1024 rows of m, pair tile of k rows, split of n).  Ring slots, barrier
+  // phases and accumulation chains are counted across items, so the next
+  // item's copies and S tiles are under way while the last chain drains.
+  const int cl = static_cast<int>(blockIdx.x >> 2);
+  const int ncl = static_cast<int>(gridDim.x >> 2);
+  const int nitems = p.nitems;
+  auto item = [&](int i) {
+    RightItem it;
+    it.z = i % p.splits;
+    const int t = i / p.splits;
+    const int64_t qt = t % p.tiles_q;
+    const int64_t mb = t / p.tiles_q;
+    it.m0 = (mb * 4 + cr) * C::ROWS;  // this CTA's rows of A
+    it.q0 = qt * nq;                  // the pair's k rows
+    it.g0 = it.q0 + static_cast<int64_t>(rank) * gh;  // this CTA's S rows
+    it.lbeg = static_cast<int64_t>(it.z) * p.chunk;
+    it.lend = min(p.L, it.lbeg + p.chunk);
+    it.nsteps = static_cast<int>((it.lend - it.lbeg + BK - 1) / BK);
+    it.nchains = (it.nsteps + CHAIN - 1) / CHAIN;
+    return it;
+  };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NS; ++i) {
@@ -1336,16 +1365,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
-      int issued = 0;
-      for (int s = 0; s < nsteps; ++s) {
-        const int so = s % C::NS;
-        // both pairs' MMAs have read the slot's previous stage
-        if (s >= C::NS && !mbar_wait(empty_o(so), ((s / C::NS) & 1) ^ 1, ab, 0x13, s)) break;
-        mbar_arrive_expect_tx(full_b(so), C::OPA);
-        tma_load_2d(sbase + C::OFF_A + so * C::OPA, &tmapA,
-                    static_cast<int32_t>(lbeg + static_cast<int64_t>(s) * BK),
-                    static_cast<int32_t>(m0), full_b(so));
-        issued = s + 1;
+      int issued = 0, g = 0;
+      bool stop = false;
+      for (int i = cl; i < nitems && !stop; i += ncl) {
+        const RightItem it = item(i);
+        for (int s = 0; s < it.nsteps; ++s, ++g) {
+          const int so = g % C::NS;
+          // both pairs' MMAs have read the slot's previous stage
+          if (g >= C::NS && !mbar_wait(empty_o(so), ((g / C::NS) & 1) ^ 1, ab, 0x13, g)) {
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(full_b(so), C::OPA);
+          tma_load_2d(sbase + C::OFF_A + so * C::OPA, &tmapA,
+                      static_cast<int32_t>(it.lbeg + static_cast<int64_t>(s) * BK),
+                      static_cast<int32_t>(it.m0), full_b(so));
+          issued = g + 1;
+        }
       }
       if (*abort_flag) {
         for (int s = max(0, issued - C::NS); s < issued; ++s)
@@ -1366,13 +1402,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint64_t a_hi = a_base & 0xFFFFFFFF00000000ull;
       const uint32_t b_lo = static_cast<uint32_t>(b_base);
       const uint64_t b_hi = b_base & 0xFFFFFFFF00000000ull;
-      int so = 0, in_chain = 0, chain_no = 0;
+      int so = 0, chain_no = 0, g = 0;
       uint32_t ph = 0;
-      for (int s = 0; s < nsteps; ++s) {
-        const bool chain_start = s == 0 || in_chain == 0;
-        if (s > 0 && in_chain == 0 && !mbar_wait(acc_empty, (chain_no - 1) & 1, ab, 0x25, s))
+      bool stop = false;
+      for (int i = cl; i < nitems && !stop; i += ncl) {
+      const int nsteps = item(i).nsteps;
+      int in_chain = 0;
+      for (int s = 0; s < nsteps; ++s, ++g) {
+        const bool chain_start = in_chain == 0;
+        // a chain starts once the epilogue has read the previous one
+        if (chain_start && chain_no > 0 &&
+            !mbar_wait(acc_empty, (chain_no - 1) & 1, ab, 0x25, g)) {
+          stop = true;
           break;
-        if (!mbar_wait(full_o(so), ph, ab, 0x22, s)) break;
+        }
+        if (!mbar_wait(full_o(so), ph, ab, 0x22, g)) {
+          stop = true;
+          break;
+        }
         tc_fence_after();
         const uint32_t a_slot = a_lo + static_cast<uint32_t>(so) * (C::OPA >> 4);
         const uint64_t bdesc = b_hi | (b_lo + static_cast<uint32_t>(so) * (C::OPS >> 4));
@@ -1389,15 +1436,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         mma_commit_pair_mask(empty_o(so), 0xF);  // all four CTAs wrote into the slot
-        if (in_chain == CHAIN - 1 || s == nsteps - 1) mma_commit_pair_mask(acc_full, pair_mask);
-        if (++in_chain == CHAIN) {
+        if (in_chain == CHAIN - 1 || s == nsteps - 1) {  // the chain ends
+          mma_commit_pair_mask(acc_full, pair_mask);
           in_chain = 0;
           ++chain_no;
+        } else {
+          ++in_chain;
         }
         if (++so == C::NS) {
           so = 0;
           ph ^= 1u;
         }
+      }
       }
       mma_commit_pair(drain_bar);
       drain_wait(drain_bar, 0, 200000000ull);
@@ -1416,17 +1466,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_BYTES);
     const int rsub = lane >> 3;       // row within a group of 4 (read side)
     const int csub = (lane & 7) * 4;  // first of 4 columns (read side)
-    if (p.tma_drain) {  // through the TMA (partial rows of whole 16-byte units)
-      for (int c0 = 0; c0 < nchains; ++c0)
+    int gc = 0;  // chains drained so far (all items)
+    bool stop = false;
+    for (int i = cl; i < nitems && !stop; i += ncl) {
+    const RightItem it = item(i);
+    const int64_t m0 = it.m0, q0 = it.q0;
+    for (int c0 = 0; c0 < it.nchains; ++c0, ++gc) {
+      if (p.tma_drain) {  // through the TMA (partial rows of whole 16-byte units)
         if (!drain_right_tma(tmem, quarter, colset, smem_u32(tile), tile, &tmapP, nq, m0, q0,
-                             static_cast<int>(blockIdx.z), c0 == 0, acc_full, lead_acc_empty, c0,
-                             ab))
+                             it.z, c0 == 0, acc_full, lead_acc_empty, gc, ab)) {
+          stop = true;
           break;
-      if (lane == 0) bulk_wait<0>();  // the last copies have completed
-    }
-    for (int c0 = 0; c0 < (p.tma_drain ? 0 : nchains); ++c0) {
-      const bool ok = mbar_wait(acc_full, c0 & 1, ab, 0x34, c0);
-      if (!__all_sync(0xffffffffu, ok)) break;
+        }
+        continue;
+      }
+      const bool ok = mbar_wait(acc_full, gc & 1, ab, 0x34, gc);
+      if (!__all_sync(0xffffffffu, ok)) {
+        stop = true;
+        break;
+      }
       tc_fence_after();
       for (int t = colset; t < 2 * nchunk; t += 2) {
         const int j = t / nchunk;
@@ -1452,7 +1510,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t gm = grow0 + rr;
           const float4 a = *reinterpret_cast<const float4*>(tile + rr * C::EPI_PITCH_R + csub);
           if (gm < p.P && c < nq) {
-            float* d = p.part + (static_cast<int64_t>(blockIdx.z) * p.P + gm) * p.Q + col;
+            float* d = p.part + (static_cast<int64_t>(it.z) * p.P + gm) * p.Q + col;
             if (vec_ok && col + 4 <= p.Q) {
               if (c0 == 0)
                 *reinterpret_cast<float4*>(d) = a;
@@ -1477,6 +1535,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
     }
+    }
+    if (p.tma_drain && lane == 0) bulk_wait<0>();  // the last copies have completed
   } else {
     // ---- workers: this CTA's half of the S tile, and its 256 rows of A ----
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
@@ -1491,22 +1551,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t w_off = static_cast<uint32_t>(gbase + 16 * wg) * 32u;
     const uint32_t w_bytes = static_cast<uint32_t>(wrows) * 32u;
     const uint32_t s_bytes = static_cast<uint32_t>(gq) * 32u;  // from all four partner warps
-    uint32_t cached_blk = 0xffffffffu;
     uint4 words = make_uint4(0u, 0u, 0u, 0u);
     int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
-    for (int s = grp; s < nsteps; s += C::NGROUPS) {
-      const int so = s % C::NS;
+    int g = 0;      // stages of the earlier items
+    bool stop = false;
+    for (int i = cl; i < nitems && !stop; i += ncl) {
+    const RightItem it = item(i);
+    const int64_t g0 = it.g0, lend = it.lend;
+    uint32_t cached_blk = 0xffffffffu;  // Philox words belong to one item's rows
+    // this group's stages of the item: g_item + s = grp (mod NGROUPS)
+    const int g_item = g;
+    for (int s = ((grp - g_item) % C::NGROUPS + C::NGROUPS) % C::NGROUPS; s < it.nsteps;
+         s += C::NGROUPS) {
+      g = g_item + s;
+      const int so = g % C::NS;
       // both pairs' MMAs have read what this CTA wrote into slot `so` (here
       // and in its partner) last time
-      bool ok = s < C::NS || mbar_wait(empty_o(so), ((s / C::NS) & 1) ^ 1, ab, 0x43, s);
-      if (!__all_sync(0xffffffffu, ok)) break;
+      bool ok = g < C::NS || mbar_wait(empty_o(so), ((g / C::NS) & 1) ^ 1, ab, 0x43, g);
+      if (!__all_sync(0xffffffffu, ok)) {
+        stop = true;
+        break;
+      }
       uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
       // the partner's half of this CTA's S rows will land here
       if (gfirst) {
         if (lane == 0) mbar_arrive_expect_tx(s_recv(so), s_bytes);
-        pend = s;
+        pend = g;
       }
-      const int64_t cbase = lbeg + static_cast<int64_t>(s) * BK;
+      const int64_t cbase = it.lbeg + static_cast<int64_t>(s) * BK;
       if (DIST == kRademacher) {
         // a lane: one row (16 wg + lane % 16) and one 8-column half (lane / 16)
         if ((lane & 15) < wrows) {
@@ -1563,8 +1635,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0 && w_bytes != 0)
         bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + w_off,
                              smem_u32(sdst) + w_off, w_bytes, partner_s_recv + 8u * so);
-      ok = mbar_wait(full_b(so), (s / C::NS) & 1, ab, 0x40, s);
-      if (!__all_sync(0xffffffffu, ok)) break;
+      ok = mbar_wait(full_b(so), (g / C::NS) & 1, ab, 0x40, g);
+      if (!__all_sync(0xffffffffu, ok)) {
+        stop = true;
+        break;
+      }
       // split the FP32 A tile in place, one 8-row group (512 bytes) per warp
       // at a time: lane = (row r = lane / 4, columns 4 (lane % 4) ..); the
       // group's hi core matrices (columns 0-7, then 8-15; 8 rows x 16 bytes)
@@ -1594,11 +1669,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // the S half and the A operands are in this CTA's own shared memory;
       // the group's first warp certifies the partner's rows too
       fence_proxy_async_smem();
-      ok = !gfirst || mbar_wait(s_recv(so), (s / C::NS) & 1, ab, 0x46, s);
-      if (!__all_sync(0xffffffffu, ok)) break;
+      ok = !gfirst || mbar_wait(s_recv(so), (g / C::NS) & 1, ab, 0x46, g);
+      if (!__all_sync(0xffffffffu, ok)) {
+        stop = true;
+        break;
+      }
       pend = -1;
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(lead_full_o + 8u * so);
+    }
+    g = g_item + it.nsteps;
     }
     // leaving early: let a copy the partner may still be sending land first
     if (gfirst && pend >= 0 && lane == 0)
@@ -2675,8 +2755,15 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   CUtensorMap pmap;
   memset(&pmap, 0, sizeof(pmap));
   p.tma_drain = encode_part_map(&pmap, p.part, s.P, s.Q, s.Q, pl.splits) ? 1 : 0;
-  dim3 grid(static_cast<unsigned>(pl.tiles_p), static_cast<unsigned>(pl.tiles_q),
-            static_cast<unsigned>(pl.splits));
+  // persistent clusters of four CTAs, as many as can be resident, each
+  // taking every NC-th item
+  p.tiles_q = static_cast<int>(pl.tiles_q);
+  p.splits = pl.splits;
+  p.nitems = static_cast<int>(pl.tiles_p / 4 * pl.tiles_q * pl.splits);
+  const int64_t resident = quad_slots() / 4;
+  const int64_t ncl = std::max<int64_t>(1, std::min<int64_t>(p.nitems, resident > 0 ? resident
+                                                                                     : p.nitems));
+  dim3 grid(static_cast<unsigned>(4 * ncl), 1, 1);
   prof_mark(h->prof_start, st);
   cudaError_t e;
   if (h->dist == kRademacher)
