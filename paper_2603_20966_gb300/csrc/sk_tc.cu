@@ -1202,12 +1202,21 @@ struct TcRightParams {
   int* status;
   uint64_t timeout_ns;
   int tma_drain;  // the partials' tensor map (kernel parameter tmapP) is valid
-  // work list: items (cluster block of 4 x 256 rows of m, pair tile of k,
-  // split of n), split fastest
-  int nitems, tiles_q, splits;
+  // work: blocks (4 x 256 rows of m, pair tile of k; tile of k fastest) of
+  // `steps` stages of n each, `units` = blocks x steps stages in all; cluster
+  // c of NC takes the stages [c units / NC, (c+1) units / NC) in block order
+  int units, steps, tiles_q;
 };
 
-// One item of the persistent right kernel, as seen by one CTA.
+// The cluster (of nc) whose share of the right kernel's stages holds stage
+// u: cluster c takes [floor(c U / nc), floor((c+1) U / nc)) (U >= nc).
+__host__ __device__ inline int64_t seg_owner(int64_t u, int64_t U, int64_t nc) {
+  return ((u + 1) * nc + U - 1) / U - 1;
+}
+
+// One segment of the persistent right kernel, as seen by one CTA: a block's
+// stages [s0, s1) within one cluster's share; z numbers the segments of the
+// block (its partial).
 struct RightItem {
   int64_t m0, q0, g0;  // first row of A, of the pair's k rows, of this CTA's S rows
   int64_t lbeg, lend;  // range of n
@@ -1309,26 +1318,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int gh = nq / 2;                                       // S rows this CTA holds
   const int gq = gh / 2;                                       // ... and generates
   const int gbase = static_cast<int>(pairi) * gq;              // from this row of them
-  // Persistent: cluster c of the grid runs items c, c + NC, ... (NC
-  // clusters), every CTA of the cluster the same list; an item is (block of
-  // 1024 rows of m, pair tile of k rows, split of n).  Ring slots, barrier
-  // phases and accumulation chains are counted across items, so the next
-  // item's copies and S tiles are under way while the last chain drains.
+  // Persistent: the stages of all blocks (1024 rows of m x a pair tile of k
+  // rows, each `steps` stages of n long) are laid end to end, and cluster c
+  // of the NC in the grid takes an equal contiguous share of them, every CTA
+  // of the cluster the same; a share is one or a few segments, one per block
+  // it touches, each summed into the partial of its place in the block.  Ring
+  // slots, barrier phases and accumulation chains are counted across
+  // segments, so the next segment's copies and S tiles are under way while
+  // the last chain drains.
   const int cl = static_cast<int>(blockIdx.x >> 2);
   const int ncl = static_cast<int>(gridDim.x >> 2);
-  const int nitems = p.nitems;
-  auto item = [&](int i) {
+  const int ubeg = static_cast<int>(static_cast<int64_t>(cl) * p.units / ncl);
+  const int uend = static_cast<int>(static_cast<int64_t>(cl + 1) * p.units / ncl);
+  auto item = [&](int u) {
     RightItem it;
-    it.z = i % p.splits;
-    const int t = i / p.splits;
-    const int64_t qt = t % p.tiles_q;
-    const int64_t mb = t / p.tiles_q;
+    const int blk = u / p.steps;
+    const int s0 = u - blk * p.steps;
+    const int s1 = min(p.steps, s0 + (uend - u));
+    it.z = static_cast<int>(cl - seg_owner(static_cast<int64_t>(blk) * p.steps, p.units, ncl));
+    const int64_t qt = blk % p.tiles_q;
+    const int64_t mb = blk / p.tiles_q;
     it.m0 = (mb * 4 + cr) * C::ROWS;  // this CTA's rows of A
     it.q0 = qt * nq;                  // the pair's k rows
     it.g0 = it.q0 + static_cast<int64_t>(rank) * gh;  // this CTA's S rows
-    it.lbeg = static_cast<int64_t>(it.z) * p.chunk;
-    it.lend = min(p.L, it.lbeg + p.chunk);
-    it.nsteps = static_cast<int>((it.lend - it.lbeg + BK - 1) / BK);
+    it.lbeg = static_cast<int64_t>(s0) * BK;
+    it.lend = min(p.L, static_cast<int64_t>(s1) * BK);
+    it.nsteps = s1 - s0;
     it.nchains = (it.nsteps + CHAIN - 1) / CHAIN;
     return it;
   };
@@ -1367,8 +1382,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       int issued = 0, g = 0;
       bool stop = false;
-      for (int i = cl; i < nitems && !stop; i += ncl) {
-        const RightItem it = item(i);
+      for (int u = ubeg; u < uend && !stop;) {
+        const RightItem it = item(u);
+        u += it.nsteps;
         for (int s = 0; s < it.nsteps; ++s, ++g) {
           const int so = g % C::NS;
           // both pairs' MMAs have read the slot's previous stage
@@ -1405,8 +1421,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int so = 0, chain_no = 0, g = 0;
       uint32_t ph = 0;
       bool stop = false;
-      for (int i = cl; i < nitems && !stop; i += ncl) {
-      const int nsteps = item(i).nsteps;
+      for (int u = ubeg; u < uend && !stop;) {
+      const int nsteps = item(u).nsteps;
+      u += nsteps;
       int in_chain = 0;
       for (int s = 0; s < nsteps; ++s, ++g) {
         const bool chain_start = in_chain == 0;
@@ -1468,8 +1485,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int csub = (lane & 7) * 4;  // first of 4 columns (read side)
     int gc = 0;  // chains drained so far (all items)
     bool stop = false;
-    for (int i = cl; i < nitems && !stop; i += ncl) {
-    const RightItem it = item(i);
+    for (int u = ubeg; u < uend && !stop;) {
+    const RightItem it = item(u);
+    u += it.nsteps;
     const int64_t m0 = it.m0, q0 = it.q0;
     for (int c0 = 0; c0 < it.nchains; ++c0, ++gc) {
       if (p.tma_drain) {  // through the TMA (partial rows of whole 16-byte units)
@@ -1555,8 +1573,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
     int g = 0;      // stages of the earlier items
     bool stop = false;
-    for (int i = cl; i < nitems && !stop; i += ncl) {
-    const RightItem it = item(i);
+    for (int u = ubeg; u < uend && !stop;) {
+    const RightItem it = item(u);
+    u += it.nsteps;
     const int64_t g0 = it.g0, lend = it.lend;
     uint32_t cached_blk = 0xffffffffu;  // Philox words belong to one item's rows
     // this group's stages of the item: g_item + s = grp (mod NGROUPS)
@@ -2715,13 +2734,69 @@ cudaError_t split_rows(const float* A, int64_t lds, int64_t m, int64_t n, void* 
   return cudaGetLastError();
 }
 
+// Segments of the persistent BF16 right kernel: blocks of 1024 rows of m x
+// a pair tile of k rows, each `steps` stages of n long, laid end to end and
+// shared equally by the `ncl` resident clusters of two CTA pairs; zmax is the
+// most segments any block is cut into, the number of partials the sketch
+// needs (2 for the 65536 x 16384, k = 256 sketch on 36 clusters, against 9
+// equal splits of n before).
+struct RightSegPlan {
+  Plan pl;  // tile geometry (nt, tmem_cols, tiles_p, tiles_q)
+  int64_t steps, units, ncl;
+  int zmax;
+};
+
+RightSegPlan plan_right_seg(const GemmShape& s) {
+  RightSegPlan r;
+  r.pl = plan_right(s);
+  r.steps = (s.L + BK - 1) / BK;
+  const int64_t blocks = r.pl.tiles_p / 4 * r.pl.tiles_q;
+  r.units = blocks * r.steps;
+  const int64_t resident = quad_slots() / 4;
+  r.ncl = std::max<int64_t>(1, std::min<int64_t>(r.units, resident));
+  r.zmax = 1;
+  for (int64_t b = 0; b < blocks; ++b) {
+    const int64_t z = seg_owner((b + 1) * r.steps - 1, r.units, r.ncl) -
+                      seg_owner(b * r.steps, r.units, r.ncl) + 1;
+    r.zmax = static_cast<int>(std::max<int64_t>(r.zmax, z));
+  }
+  return r;
+}
+
+// Y = scale x the sum, in segment order, of the partials of each element's
+// block (as many as segments the block was cut into).  CUDA block (x, y)
+// takes rows y * 1024 + x, + gridDim.x, ... of block row y; a thread keeps
+// its columns (and so its blocks' segment counts) for all of them.
+__global__ void __launch_bounds__(256)
+    k_reduce_segments(const float* __restrict__ part, int64_t P, int64_t Q, int nq, int tiles_q,
+                      int64_t steps, int64_t units, int64_t ncl, float scale,
+                      float* __restrict__ Y, int64_t ldy) {
+  const int64_t total = P * Q;
+  const int64_t mblocks = (P + 4 * CfgR::ROWS - 1) / (4 * CfgR::ROWS);
+  for (int64_t mb = blockIdx.y; mb < mblocks; mb += gridDim.y) {
+    const int64_t r0 = mb * (4 * CfgR::ROWS);
+    const int64_t r1 = min(P, r0 + 4 * CfgR::ROWS);
+    for (int64_t c = threadIdx.x; c < Q; c += blockDim.x) {
+      const int64_t blk = mb * tiles_q + c / nq;
+      const int64_t nseg =
+          seg_owner((blk + 1) * steps - 1, units, ncl) - seg_owner(blk * steps, units, ncl) + 1;
+      for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const int64_t i = r * Q + c;
+        float acc = 0.0f;
+        for (int64_t z = 0; z < nseg; ++z) acc = __fadd_rn(acc, part[z * total + i]);
+        Y[r * ldy + c] = __fmul_rn(scale, acc);
+      }
+    }
+  }
+}
+
 size_t tc_workspace_bytes(const GemmShape& s) {
   if (s.left) {
     const LeftPlan pl = plan_left(s);
     return split_bytes(s.L, s.Q) + static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
   }
-  const Plan pl = plan_right(s);
-  return static_cast<size_t>(pl.splits) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
+  const RightSegPlan rs = plan_right_seg(s);
+  return static_cast<size_t>(rs.zmax) * static_cast<size_t>(s.P) * static_cast<size_t>(s.Q) *
          sizeof(float);
 }
 
@@ -2735,7 +2810,8 @@ sk_status tc_check(const GemmShape& s, const float* A, int64_t lda, const float*
 
 cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float* A, int64_t lda,
                             float* Y, int64_t ldy, void* ws, size_t ws_bytes, cudaStream_t st) {
-  const Plan pl = plan_right(s);
+  const RightSegPlan rs = plan_right_seg(s);
+  const Plan& pl = rs.pl;
   CUtensorMap map;
   // A[m x n]: n innermost; one box = 16 columns of n x 256 rows of m
   if (!encode_map(&map, A, s.P, s.L, lda, BK, CfgR::ROWS)) return cudaErrorInvalidValue;
@@ -2749,21 +2825,19 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   p.rk = round_keys(make_key(h->seed));
   p.status = h->d_status;
   p.timeout_ns = h->wait_limit_ns;
-  const size_t need = static_cast<size_t>(pl.splits) * s.P * s.Q * sizeof(float);
+  const size_t need = static_cast<size_t>(rs.zmax) * s.P * s.Q * sizeof(float);
   if (ws == nullptr || ws_bytes < need) return cudaErrorInvalidValue;
   p.part = static_cast<float*>(ws);
   CUtensorMap pmap;
   memset(&pmap, 0, sizeof(pmap));
-  p.tma_drain = encode_part_map(&pmap, p.part, s.P, s.Q, s.Q, pl.splits) ? 1 : 0;
+  p.tma_drain = encode_part_map(&pmap, p.part, s.P, s.Q, s.Q, rs.zmax) ? 1 : 0;
   // persistent clusters of four CTAs, as many as can be resident, each
-  // taking every NC-th item
+  // taking an equal contiguous share of the stages
+  if (rs.units > (int64_t(1) << 31) - 1) return cudaErrorInvalidValue;  // 32-bit stage numbers
   p.tiles_q = static_cast<int>(pl.tiles_q);
-  p.splits = pl.splits;
-  p.nitems = static_cast<int>(pl.tiles_p / 4 * pl.tiles_q * pl.splits);
-  const int64_t resident = quad_slots() / 4;
-  const int64_t ncl = std::max<int64_t>(1, std::min<int64_t>(p.nitems, resident > 0 ? resident
-                                                                                     : p.nitems));
-  dim3 grid(static_cast<unsigned>(4 * ncl), 1, 1);
+  p.steps = static_cast<int>(rs.steps);
+  p.units = static_cast<int>(rs.units);
+  dim3 grid(static_cast<unsigned>(4 * rs.ncl), 1, 1);
   prof_mark(h->prof_start, st);
   cudaError_t e;
   if (h->dist == kRademacher)
@@ -2775,7 +2849,17 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   prof_mark(h->prof_stop, st);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  return splitk_reduce(static_cast<float*>(ws), pl.splits, s.P, s.Q, h->scale, Y, ldy, st);
+  const int64_t mblocks = pl.tiles_p / 4;  // blocks of 1024 rows of m
+  const int64_t per = std::max<int64_t>(
+      1, std::min<int64_t>(4 * CfgR::ROWS,
+                           static_cast<int64_t>(num_sms_tc()) * 16 / std::max<int64_t>(1, mblocks)));
+  k_reduce_segments<<<dim3(static_cast<unsigned>(per),
+                           static_cast<unsigned>(std::min<int64_t>(mblocks, 65535))),
+                      256, 0, st>>>(
+      static_cast<const float*>(ws), s.P, s.Q, pl.nt, p.tiles_q, rs.steps, rs.units, rs.ncl,
+      h->scale, Y, ldy);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 int64_t q8_ld(int64_t n) { return (n + 15) / 16 * 16; }
