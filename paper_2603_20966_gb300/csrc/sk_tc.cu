@@ -1193,9 +1193,8 @@ struct CfgR {
 };
 
 struct TcRightParams {
-  float* part;      // partials [splits][P][Q]
+  float* part;      // partials [segments][P][Q] (a block's segments in order)
   int64_t P, Q, L;  // P = m, Q = k, L = n
-  int64_t chunk;    // contracted length per split (multiple of BK)
   int nq;           // N of the MMA: k rows per pair tile (multiple of 16, <= 256)
   int tmem_cols;    // power of two >= 2 * nq
   PhiloxRoundKeys rk;
@@ -2819,7 +2818,6 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   p.P = s.P;
   p.Q = s.Q;
   p.L = s.L;
-  p.chunk = pl.chunk;
   p.nq = pl.nt;
   p.tmem_cols = pl.tmem_cols;
   p.rk = round_keys(make_key(h->seed));
