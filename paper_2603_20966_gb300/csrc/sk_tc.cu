@@ -1740,7 +1740,9 @@ struct CfgQ {
   static constexpr uint32_t OFF_S = OFF_A + NSO * OPA;
   static constexpr uint32_t OFF_EPI = OFF_S + NSO * OPS;  // epilogue transpose tiles
   static constexpr uint32_t OFF_BAR = OFF_EPI + NUM_EPI_WARPS * EPI_TILE;
-  static constexpr uint32_t NUM_BARS = 3 * NSO + 3;
+  // per slot: A landed, operands ready, slot read by both pairs' MMAs, S rows
+  // received from the partner CTA; then the accumulator and drain barriers
+  static constexpr uint32_t NUM_BARS = 4 * NSO + 3;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NUM_BARS * 8;
   static constexpr uint32_t SMEM = OFF_MISC + 16 + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
@@ -1789,7 +1791,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto full_a = [&](int i) { return bar0 + 8u * i; };
   auto full_o = [&](int i) { return bar0 + 8u * (C::NSO + i); };
   auto empty_o = [&](int i) { return bar0 + 8u * (2 * C::NSO + i); };
-  const uint32_t acc_full = bar0 + 8u * (3 * C::NSO);
+  auto s_recv = [&](int i) { return bar0 + 8u * (3 * C::NSO + i); };
+  const uint32_t acc_full = bar0 + 8u * (4 * C::NSO);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain_bar = acc_full + 16u;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC);
@@ -1797,10 +1800,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_ctarank() & 1u;  // 0 = even CTA (MMA issuer)
+  // a cluster holds two CTA pairs (cluster ranks 0-1 and 2-3) with the same
+  // k rows and the same range of n on consecutive rows of m; the two CTAs of
+  // equal rank hold the same rows of the S tile, and each generates half of
+  // them and copies that half into its partner (as in the BF16 right sketch)
+  const uint32_t cr = cluster_ctarank();
+  const uint32_t rank = cr & 1u;  // 0 = even CTA of the pair (MMA issuer)
+  const uint32_t pairi = cr >> 1;
+  const uint32_t lead_rank = cr & ~1u;  // the pair's even CTA
+  const uint32_t partner = cr ^ 2u;     // same rank, other pair
   const bool leader = rank == 0;
   const int nq = p.nq;
-  const int gh = nq / 2;                                          // S rows this CTA generates
+  const int gh = nq / 2;                          // S rows this CTA holds
+  const int gq = gh / 2;                          // ... and generates (whole 8-row groups)
+  const int gbase = static_cast<int>(pairi) * gq; // from this row of them
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * C::ROWS;  // this CTA's rows of A
   const int64_t q0 = static_cast<int64_t>(blockIdx.y) * nq;       // the pair's k rows
   const int64_t g0 = q0 + static_cast<int64_t>(rank) * gh;        // this CTA's S rows
@@ -1813,7 +1826,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < C::NSO; ++i) {
       mbar_init(full_a(i), 1);
       mbar_init(full_o(i), C::GROUP_WARPS * 2);
-      mbar_init(empty_o(i), 1);
+      mbar_init(empty_o(i), 2);  // the MMAs of both pairs read what this CTA wrote
+      mbar_init(s_recv(i), 1);   // the receiving group's expect-tx, plus the copy's bytes
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_EPI_WARPS * 2);
@@ -1832,8 +1846,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const Abort ab{abort_flag, p.status, p.timeout_ns};
-  const uint32_t lead_full_o = mapa_shared(full_o(0), 0u);
-  const uint32_t lead_acc_empty = mapa_shared(acc_empty, 0u);
+  const uint32_t lead_full_o = mapa_shared(full_o(0), lead_rank);
+  const uint32_t lead_acc_empty = mapa_shared(acc_empty, lead_rank);
+  const uint32_t partner_s_recv = mapa_shared(s_recv(0), partner);
+  const uint32_t partner_s = mapa_shared(sbase + C::OFF_S, partner);
+  const uint16_t pair_mask = static_cast<uint16_t>(3u << (2u * pairi));
 
   if (warp == WARP_TMA) {
     if (lane == 0) {
@@ -1878,8 +1895,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           (in_chain > 0 || ks > 0) ? 1u : 0u);
           }
         }
-        mma_commit_pair_both(empty_o(so));
-        if (in_chain == QCHAIN - 1 || s == nsteps - 1) mma_commit_pair_both(acc_full);
+        mma_commit_pair_mask(empty_o(so), 0xF);  // all four CTAs wrote into the slot
+        if (in_chain == QCHAIN - 1 || s == nsteps - 1) mma_commit_pair_mask(acc_full, pair_mask);
       }
       mma_commit_pair(drain_bar);
       drain_wait(drain_bar, 0, 200000000ull);
@@ -1957,17 +1974,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ---- workers: this CTA's half of the E4M3 S tile [gh x 128] ----
+    // Each warp generates whole 8-row groups (1024 contiguous bytes each in
+    // the tile layout) of this CTA's generated rows and copies each into the
+    // partner itself, so no barrier spans the group.
     const int grp = (warp - WARP_WORK0) / C::GROUP_WARPS;
     const int wt = threadIdx.x - 32 * WARP_WORK0 - grp * C::GROUP_THREADS;
+    const int wg = wt >> 5;       // warp of the group
+    const bool gfirst = wg == 0;  // registers the expected bytes and waits for them
+    const uint32_t s_bytes = static_cast<uint32_t>(gq) * QK;  // from all four partner warps
+    const int ngroups8 = gq / 8;
+    int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
     for (int s = grp; s < nsteps; s += C::NGROUPS) {
       const int so = s % C::NSO;
+      // both pairs' MMAs have read what this CTA wrote into slot `so` (here
+      // and in its partner) last time
       bool ok = s < C::NSO || mbar_wait(empty_o(so), ((s / C::NSO) & 1) ^ 1, ab, 0x43, s);
       if (!__all_sync(0xffffffffu, ok)) break;
       uint8_t* sdst = smem + C::OFF_S + so * C::OPS;
+      if (gfirst) {  // the partner's half of this CTA's S rows will land here
+        if (lane == 0) mbar_arrive_expect_tx(s_recv(so), s_bytes);
+        pend = s;
+      }
       const int64_t cbase = lbeg + static_cast<int64_t>(s) * QK;  // a multiple of 128
-      if (DIST == kRademacher) {
-        // one row per task: one Philox call covers the stage's 128 columns
-        for (int r = wt; r < gh; r += C::GROUP_THREADS) {
+      for (int rg = wg; rg < ngroups8; rg += C::GROUP_WARPS) {
+        const uint32_t r8 = static_cast<uint32_t>(gbase + 8 * rg);  // first row of the group
+        if (DIST == kRademacher) {
+          // a lane: one row (lane % 8) and one quarter of the stage's 128
+          // columns (lane / 8); one Philox call covers the row's 128 columns
+          const uint32_t r = r8 + (static_cast<uint32_t>(lane) & 7u);
+          const uint32_t qc = static_cast<uint32_t>(lane) >> 3;
           const int64_t grow = g0 + r;
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
           int64_t nv = 0;
@@ -1976,10 +2011,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 static_cast<uint32_t>(cbase >> 7), 0u);
             nv = min(lend - cbase, static_cast<int64_t>(QK));
           }
-          const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+          const uint32_t word = qc == 0 ? w.x : qc == 1 ? w.y : qc == 2 ? w.z : w.w;
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {  // 16-column blocks
-            const uint32_t bits = words[b >> 1] >> (16 * (b & 1));
+          for (int b2 = 0; b2 < 2; ++b2) {  // the quarter's two 16-column blocks
+            const uint32_t bits = word >> (16 * b2);
+            const int b = 2 * static_cast<int>(qc) + b2;
             uint32_t q[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -1992,40 +2028,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 q[u] &= keep;
               }
             }
-            *reinterpret_cast<uint4*>(sdst + q8_off(static_cast<uint32_t>(r), 16u * b)) =
+            *reinterpret_cast<uint4*>(sdst + q8_off(r, 16u * b)) =
                 make_uint4(q[0], q[1], q[2], q[3]);
           }
-        }
-      } else {
-        // per 32 tasks: 8 rows x 4 quads of one 16-column block
-        const int ntasks = gh * 32;
-#pragma unroll 2
-        for (int t = wt; t < ntasks; t += C::GROUP_THREADS) {
-          const uint32_t l = static_cast<uint32_t>(t & 31);
-          const uint32_t w = static_cast<uint32_t>(t >> 5);
-          const uint32_t blk = w & 7u;
-          const uint32_t r = (w >> 3) * 8u + (l >> 2);
-          const uint32_t c = blk * 16u + (l & 3u) * 4u;
+        } else {
+          // 256 tasks of 4 entries: lane l takes row l / 4 and quad l % 4 of
+          // each of the 8 16-column blocks (a warp's 4-byte stores of a block
+          // fill its 128 contiguous bytes)
+          const uint32_t r = r8 + (static_cast<uint32_t>(lane) >> 2);
           const int64_t grow = g0 + r;
-          const int64_t cc = cbase + c;
-          uint32_t q = 0u;
-          if (grow < p.Q && cc < lend) {
-            const float4 a = DIST == kUniform
-                                 ? uniform4(p.rk, static_cast<uint32_t>(grow),
-                                            static_cast<uint32_t>(cc >> 2), 0u)
-                                 : gaussian4(p.rk, static_cast<uint32_t>(grow),
-                                             static_cast<uint32_t>(cc >> 2), 0u);
-            q = e4m3x4(a);
+#pragma unroll 2
+          for (int b = 0; b < 8; ++b) {
+            const uint32_t c = static_cast<uint32_t>(b) * 16u + (static_cast<uint32_t>(lane) & 3u) * 4u;
+            const int64_t cc = cbase + c;
+            uint32_t q = 0u;
+            if (grow < p.Q && cc < lend) {
+              const float4 a = DIST == kUniform
+                                   ? uniform4(p.rk, static_cast<uint32_t>(grow),
+                                              static_cast<uint32_t>(cc >> 2), 0u)
+                                   : gaussian4(p.rk, static_cast<uint32_t>(grow),
+                                               static_cast<uint32_t>(cc >> 2), 0u);
+              q = e4m3x4(a);
+            }
+            *reinterpret_cast<uint32_t*>(sdst + q8_off(r, c)) = q;
           }
-          *reinterpret_cast<uint32_t*>(sdst + q8_off(r, c)) = q;
         }
+        // the group's rows are written: copy them into the partner (async
+        // proxy, completing on its s_recv barrier)
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0)
+          bulk_copy_to_cluster(partner_s + static_cast<uint32_t>(so) * C::OPS + r8 * 128u,
+                               smem_u32(sdst) + r8 * 128u, 1024u, partner_s_recv + 8u * so);
       }
       ok = mbar_wait(full_a(so), (s / C::NSO) & 1, ab, 0x40, s);
       if (!__all_sync(0xffffffffu, ok)) break;
-      fence_proxy_async_smem();  // the S tile is read by the tensor core
+      // this CTA's own rows are fenced above; the group's first warp
+      // certifies the partner's rows too
+      ok = !gfirst || mbar_wait(s_recv(so), (s / C::NSO) & 1, ab, 0x46, s);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      pend = -1;
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(lead_full_o + 8u * so);
     }
+    // leaving early: let a copy the partner may still be sending land first
+    if (gfirst && pend >= 0 && lane == 0)
+      drain_wait(s_recv(pend % C::NSO), (pend / C::NSO) & 1, 100000000ull);
   }
 
   tc_fence_before();
@@ -2614,10 +2662,11 @@ Plan plan_right(const GemmShape& s, int cluster = 4) {
   return pl;
 }
 
-// FP8 right sketch: the same tiling as the BF16 right sketch, splits of
-// whole 128-column stages.
+// FP8 right sketch: the same tiling as the BF16 right sketch (clusters of
+// two CTA pairs sharing each generated S tile), splits of whole 128-column
+// stages.
 Plan plan_right_q(const GemmShape& s) {
-  Plan pl = plan_right(s, 2);
+  Plan pl = plan_right(s, 4);
   int64_t chunk = (s.L + pl.splits - 1) / pl.splits;
   chunk = (chunk + QK - 1) / QK * QK;
   pl.chunk = chunk;
@@ -2647,7 +2696,7 @@ cudaError_t launch_right_q(const CUtensorMap& map, const TcRightQParams& p, dim3
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  fill_config<true>(&cfg, attr, grid, st);
+  fill_config<true>(&cfg, attr, grid, st, 4);
   cfg.dynamicSmemBytes = CfgQ::SMEM;
   return cudaLaunchKernelEx(&cfg, k_sketch_e4m3_right<DIST>, map, p);
 }
