@@ -1151,14 +1151,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // chains and bounded waits are those of the left kernel.
 //
 // One ring of stages: the TMA brings a stage's FP32 A tile [256 rows][16]
-// into the slot, and the workers split it in place.  The 512 bytes of an
-// 8-row group of the FP32 tile become that group's K-major BF16 core
-// matrices, hi (256 bytes: 8 rows x 2 halves of 8 columns) then lo, so a warp
-// converts one group with no other warp involved, and the MMA reads hi and lo
-// with 512 bytes between 8-row groups.  With no separate staging ring the
-// slots are 20 KB and the ring is 8 stages deep, so up to 128 KB of A per SM
-// are in flight from HBM.  The kernel is persistent: as many clusters as can
-// be resident each run every NC-th item of the work list, with ring slots,
+// into the slot (64-byte swizzle), and the workers split it in place.  The
+// 512 bytes of an 8-row group of the FP32 tile become that group's K-major
+// BF16 core matrices, hi (256 bytes: 8 rows x 2 halves of 8 columns) then
+// lo, so a warp converts whole groups with no other warp involved, and the
+// MMA reads hi and lo with 512 bytes between 8-row groups.  With no separate
+// staging ring the slots are 20 KB and the ring is 8 stages deep, so up to
+// 128 KB of A per SM are in flight from HBM.  The kernel is persistent: as
+// many clusters as can be resident each take an equal contiguous share of
+// the stages of all blocks, with ring slots,
 // barrier phases and chains counted across items, so the next item's copies
 // and S tiles are under way while the last chain of the previous one drains.
 // ---------------------------------------------------------------------------
@@ -1658,30 +1659,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         stop = true;
         break;
       }
-      // split the FP32 A tile in place, one 8-row group (512 bytes) per warp
-      // at a time: lane = (row r = lane / 4, columns 4 (lane % 4) ..); the
-      // group's hi core matrices (columns 0-7, then 8-15; 8 rows x 16 bytes)
-      // replace its first 256 bytes, lo its last 256
+      // split the FP32 A tile in place, two 8-row groups (512 bytes each) per
+      // warp at a time: lane = (group lane / 16, row r = lane % 8, columns
+      // 8 h .. 8 h + 7 with h = (lane / 8) % 2).  The TMA lands each 64-byte
+      // row with the 64-byte swizzle (16-byte unit u of row r at
+      // u ^ ((r / 2) mod 4)), so the 8 lanes of a load phase read 8 different
+      // bank groups; the row's hi core-matrix row (8 columns, 16 bytes)
+      // replaces bytes 128 h + 16 r of the group, its lo row 256 bytes
+      // further, so the 8 lanes of a store phase write 128 contiguous bytes
       {
         uint8_t* slot = smem + C::OFF_A + so * C::OPA;
-        const uint32_t r = static_cast<uint32_t>(lane) >> 2;
-        const uint32_t c4 = static_cast<uint32_t>(lane) & 3u;
-        const uint32_t dst = (c4 >> 1) * 128u + r * 16u + (c4 & 1u) * 8u;
+        const uint32_t r = static_cast<uint32_t>(lane) & 7u;
+        const uint32_t h = (static_cast<uint32_t>(lane) >> 3) & 1u;
+        const uint32_t sw = (r >> 1) & 3u;
+        const uint32_t ld0 = r * 64u + (((2u * h) ^ sw) << 4);
+        const uint32_t ld1 = r * 64u + (((2u * h + 1u) ^ sw) << 4);
+        const uint32_t dst = h * 128u + r * 16u;
 #pragma unroll 2
-        for (int gi = wg; gi < C::ROWS / 8; gi += C::GROUP_WARPS) {
+        for (int gi = 2 * wg + (lane >> 4); gi < C::ROWS / 8; gi += 2 * C::GROUP_WARPS) {
           uint8_t* grp8 = slot + gi * C::GROUP_A;
-          const float4 x = *reinterpret_cast<const float4*>(grp8 + r * 64u + c4 * 16u);
-          __syncwarp();  // the warp's group has been read
+          const float4 x = *reinterpret_cast<const float4*>(grp8 + ld0);
+          const float4 y = *reinterpret_cast<const float4*>(grp8 + ld1);
+          __syncwarp();  // the warp's groups have been read
           const uint32_t h0 = pack_bf16x2(x.x, x.y), h1 = pack_bf16x2(x.z, x.w);
-          // a - hi of both elements in one packed FMA (the product by -1 is
+          const uint32_t h2 = pack_bf16x2(y.x, y.y), h3 = pack_bf16x2(y.z, y.w);
+          // a - hi of two elements in one packed FMA (the product by -1 is
           // exact, so each component is the rounded difference)
           const float2 l0 = __ffma2_rn(f2(__uint_as_float(h0 << 16), __uint_as_float(h0 & 0xffff0000u)),
                                        f2(-1.0f, -1.0f), f2(x.x, x.y));
           const float2 l1 = __ffma2_rn(f2(__uint_as_float(h1 << 16), __uint_as_float(h1 & 0xffff0000u)),
                                        f2(-1.0f, -1.0f), f2(x.z, x.w));
-          *reinterpret_cast<uint2*>(grp8 + dst) = make_uint2(h0, h1);
-          *reinterpret_cast<uint2*>(grp8 + 256u + dst) =
-              make_uint2(pack_bf16x2(l0.x, l0.y), pack_bf16x2(l1.x, l1.y));
+          const float2 l2 = __ffma2_rn(f2(__uint_as_float(h2 << 16), __uint_as_float(h2 & 0xffff0000u)),
+                                       f2(-1.0f, -1.0f), f2(y.x, y.y));
+          const float2 l3 = __ffma2_rn(f2(__uint_as_float(h3 << 16), __uint_as_float(h3 & 0xffff0000u)),
+                                       f2(-1.0f, -1.0f), f2(y.z, y.w));
+          *reinterpret_cast<uint4*>(grp8 + dst) = make_uint4(h0, h1, h2, h3);
+          *reinterpret_cast<uint4*>(grp8 + 256u + dst) =
+              make_uint4(pack_bf16x2(l0.x, l0.y), pack_bf16x2(l1.x, l1.y),
+                         pack_bf16x2(l2.x, l2.y), pack_bf16x2(l3.x, l3.y));
         }
       }
       // the S half and the A operands are in this CTA's own shared memory;
@@ -2270,7 +2285,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // Row-major FP32 matrix [rows x cols] (cols innermost) with boxes of
 // {box_cols, box_rows}; zero fill outside the matrix.
 bool encode_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld,
-                int box_cols, int box_rows) {
+                int box_cols, int box_rows,
+                CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (enc == nullptr) return false;
   const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
@@ -2278,7 +2294,7 @@ bool encode_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estride[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride,
-             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -2861,8 +2877,10 @@ cudaError_t tc_sketch_right(const sk_sketch* h, const GemmShape& s, const float*
   const RightSegPlan rs = plan_right_seg(s);
   const Plan& pl = rs.pl;
   CUtensorMap map;
-  // A[m x n]: n innermost; one box = 16 columns of n x 256 rows of m
-  if (!encode_map(&map, A, s.P, s.L, lda, BK, CfgR::ROWS)) return cudaErrorInvalidValue;
+  // A[m x n]: n innermost; one box = 16 columns of n x 256 rows of m, each
+  // 64-byte row with the 64-byte swizzle (the in-place split's lane map)
+  if (!encode_map(&map, A, s.P, s.L, lda, BK, CfgR::ROWS, CU_TENSOR_MAP_SWIZZLE_64B))
+    return cudaErrorInvalidValue;
   TcRightParams p;
   p.P = s.P;
   p.Q = s.Q;
