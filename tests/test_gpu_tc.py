@@ -42,6 +42,8 @@ def run_left(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
         assert P.sk_stream_status(h) == 0
     finally:
         P.sk_destroy(h)
+    # the padding columns of Y's rows are never written
+    assert torch.isnan(Y[:, n:]).all()
     return Y[:, :n].cpu().numpy()
 
 
@@ -190,13 +192,17 @@ def run_right(P, seed, dist, k, A, prec=BF16, lda=None, ldy=None):
         assert P.sk_stream_status(h) == 0
     finally:
         P.sk_destroy(h)
+    # the padding columns of Y's rows are never written
+    assert torch.isnan(Y[:, k:]).all()
     return Y[:, :k].cpu().numpy()
 
 
 # k tiles of 32 to 256 rows (each CTA pair's S tile split between the two
 # pairs of a cluster in whole 8-row groups), including 96 and 224
 RIGHT_SHAPES = [(512, 4096, 256), (1000, 3000, 100), (300, 17, 31), (5, 5, 3), (2048, 1000, 512),
-                (700, 70000, 48), (4096, 2048, 256), (3000, 2000, 200), (2500, 1500, 90)]
+                (700, 70000, 48), (4096, 2048, 256), (3000, 2000, 200), (2500, 1500, 90),
+                # more 1024-row blocks than clusters, two tiles of k, ragged m
+                (40000, 600, 300)]
 
 
 @pytest.mark.parametrize("dist", [R, G])
