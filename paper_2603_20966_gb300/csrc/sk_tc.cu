@@ -1483,7 +1483,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float* tile = reinterpret_cast<float*>(smem + C::OFF_EPI + (warp - WARP_EPI0) * C::EPI_BYTES);
     const int rsub = lane >> 3;       // row within a group of 4 (read side)
     const int csub = (lane & 7) * 4;  // first of 4 columns (read side)
-    int gc = 0;  // chains drained so far (all items)
+    int gc = 0;  // chains drained so far (all segments)
     bool stop = false;
     for (int u = ubeg; u < uend && !stop;) {
     const RightItem it = item(u);
@@ -1571,14 +1571,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t s_bytes = static_cast<uint32_t>(gq) * 32u;  // from all four partner warps
     uint4 words = make_uint4(0u, 0u, 0u, 0u);
     int pend = -1;  // a stage whose copy into this CTA was expected, not yet waited for
-    int g = 0;      // stages of the earlier items
+    int g = 0;      // stages of the earlier segments
     bool stop = false;
     for (int u = ubeg; u < uend && !stop;) {
     const RightItem it = item(u);
     u += it.nsteps;
     const int64_t g0 = it.g0, lend = it.lend;
-    uint32_t cached_blk = 0xffffffffu;  // Philox words belong to one item's rows
-    // this group's stages of the item: g_item + s = grp (mod NGROUPS)
+    uint32_t cached_blk = 0xffffffffu;  // Philox words belong to one segment's rows
+    // this group's stages of the segment: g_item + s = grp (mod NGROUPS)
     const int g_item = g;
     for (int s = ((grp - g_item) % C::NGROUPS + C::NGROUPS) % C::NGROUPS; s < it.nsteps;
          s += C::NGROUPS) {
